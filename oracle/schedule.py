@@ -1,0 +1,330 @@
+"""Optimal SRJ parameters, integer conversion and cycle ordering (oracle side).
+
+TEST INFRASTRUCTURE: only the tests, the smoke check, the CPU-baseline leg of
+the benchmark and ``oracle/make_schedules.py`` use this module.
+
+Paper: Adsuara et al., "Scheduled Relaxation Jacobi method: improvements and
+applications", arXiv:1511.04292.  Notation follows the paper: P levels, weights
+omega_1 > ... > omega_P, fractions beta_i (sum 1), integer repetitions q_i,
+M = sum q_i, spectral variable kappa in [kappa_m, kappa_M = 2].
+
+* ``log_gamma``           Eq. Gamma (per-iteration amplification, in logs).
+* ``beta_theorem2``       Theorem 2, Eq. betai: beta from omega and the interior
+                          maxima kappa_1..kappa_{P-1}.
+* ``system``              the reduced system S(omega, kappa) of Sect. 3.5:
+                          equal maxima (Eq. equMax) plus the optimality
+                          conditions of Eqs. partialbeta / equDifBeta, imposed
+                          through Lagrange multipliers (see ``system``).
+* ``initial_guess``       Eqs. omegaaprox1 / omegaaprox2 and the kappa_i guess
+                          of Sect. 3.5.
+* ``solve_optimal``       continuation in P (Sect. 3.3: weights of P+1 levels
+                          from the extrapolated extreme weights of P-3..P).
+* ``q_floor``             Sect. 4.3: q_i = floor(beta_i / beta_1).
+* ``rho``                 Eq. rho.
+* ``order_drift``         cycle ordering (Sect. 5.1 asks for the large
+                          over-relaxations to be spread over the cycle; the
+                          algorithm is this build's reading, see its docstring).
+"""
+from __future__ import annotations
+
+import math
+import warnings
+
+import numpy as np
+from scipy import optimize
+
+KAPPA_MAX = 2.0
+
+
+# ---------------------------------------------------------------------------
+# Amplification factors
+# ---------------------------------------------------------------------------
+
+def log_gamma(kappa, omega, beta):
+    """log Gamma(kappa) = sum_i beta_i log|1 - omega_i kappa| (Eq. Gamma)."""
+    kappa = np.atleast_1d(np.asarray(kappa, dtype=np.float64))
+    omega = np.asarray(omega, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    return np.log(np.abs(1.0 - np.outer(kappa, omega))) @ beta
+
+
+def log10_cycle_factor(kappa, omega, q):
+    """log10 |prod_i G_{omega_i}(kappa)^{q_i}| for one M-cycle (Eq. cycleAmplFact)."""
+    kappa = np.atleast_1d(np.asarray(kappa, dtype=np.float64))
+    return np.log10(np.abs(1.0 - np.outer(kappa, np.asarray(omega, float)))) @ np.asarray(q, float)
+
+
+def rho(omega, beta):
+    """Convergence performance index rho = sum_i omega_i beta_i (Eq. rho)."""
+    return float(np.dot(omega, beta))
+
+
+def beta_theorem2(omega, kappa_int):
+    """Theorem 2 (Eq. betai), with the products over k and l taken separately:
+
+        beta_i = prod_{k=1}^{P-1} (1 - kappa_k omega_i) * prod_{l != i} omega_l / (omega_l - omega_i).
+    """
+    omega = np.asarray(omega, dtype=np.float64)
+    P = len(omega)
+    beta = np.empty(P)
+    for i in range(P):
+        v = 1.0
+        for kk in kappa_int:
+            v *= 1.0 - kk * omega[i]
+        for l in range(P):
+            if l != i:
+                v *= omega[l] / (omega[l] - omega[i])
+        beta[i] = v
+    return beta
+
+
+def interior_maxima(omega, beta):
+    """Roots of d log Gamma / d kappa = 0 (Eq. partialG), one in each
+    (1/omega_i, 1/omega_{i+1}) (Sect. 3.5)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    out = []
+    for i in range(len(omega) - 1):
+        lo, hi = 1.0 / omega[i], 1.0 / omega[i + 1]
+        g = lambda k: float(np.sum(beta * omega / (1.0 - k * omega)))
+        a, b = lo * (1 + 1e-13), hi * (1 - 1e-13)
+        out.append(optimize.brentq(g, a, b, xtol=1e-300, rtol=1e-15, maxiter=500))
+    return np.array(out)
+
+
+# ---------------------------------------------------------------------------
+# The system S(omega, kappa)
+# ---------------------------------------------------------------------------
+
+def _unpack(x, P):
+    """x = (log omega_1..P, t_1..t_{P-1}); kappa_i = 1/omega_i + s(t_i) (1/omega_{i+1} - 1/omega_i)
+    with s the logistic function, so each kappa_i stays inside its bracket (Sect. 3.5)."""
+    omega = np.exp(x[:P])
+    s = 0.5 * (1.0 + np.tanh(0.5 * np.asarray(x[P:], dtype=np.float64)))
+    inv = 1.0 / omega
+    return omega, inv[:-1] + s * (inv[1:] - inv[:-1])
+
+
+def _pack(omega, kint):
+    inv = 1.0 / np.asarray(omega, dtype=np.float64)
+    s = (np.asarray(kint) - inv[:-1]) / (inv[1:] - inv[:-1])
+    s = np.clip(s, 1e-12, 1 - 1e-12)
+    return np.concatenate([np.log(omega), np.log(s / (1.0 - s))])
+
+
+def system(x, P, kappa_m):
+    """Residuals of the reduced system S(omega, kappa) (Sect. 3.5).
+
+    Unknowns x = (log omega_1..omega_P, t_1..t_{P-1}) with kappa_i placed inside
+    (1/omega_i, 1/omega_{i+1}) by t_i (see ``_unpack``); beta follows from
+    Theorem 2, so the interior kappa_i are stationary points of Gamma (Eq.
+    partialG) by construction.  With kappa_0 = kappa_m and kappa_P = 2:
+
+    * P equations, Eq. equMax: log Gamma(kappa_j) - log Gamma(kappa_0) = 0, j=1..P.
+    * P-1 optimality equations.  Eqs. partialbeta / equDifBeta ask that the
+      common level of the maxima be stationary in beta when omega moves to keep
+      the maxima equal.  This is imposed in its Lagrange-multiplier form: there
+      are weights mu_0..mu_P (sum 1) on the active points with
+      sum_j mu_j kappa_j / (1 - omega_i kappa_j) = 0 for every i (stationarity
+      in omega), and sum_j mu_j (log|1-omega_i kappa_j| - log|1-omega_P kappa_j|)
+      = 0 for i = 1..P-1 (stationarity in beta on the simplex).
+    """
+    omega, kint = _unpack(x, P)
+    beta = beta_theorem2(omega, kint)
+    kap = np.concatenate([[kappa_m], kint, [KAPPA_MAX]])
+    F = log_gamma(kap, omega, beta)
+    eq_max = F[1:] - F[0]
+    Mm = np.vstack([kap[None, :] / (1.0 - np.outer(omega, kap)), np.ones((1, P + 1))])
+    rhs = np.zeros(P + 1)
+    rhs[-1] = 1.0
+    mu = np.linalg.solve(Mm, rhs)
+    a = np.log(np.abs(1.0 - np.outer(omega, kap)))
+    eq_opt = (a[:-1, :] - a[-1:, :]) @ mu
+    return np.concatenate([eq_max, eq_opt])
+
+
+def guess_exponents(P):
+    """Exponents e of the initial inverse weights omega_1^-1 (omega_1/omega_P)^e,
+    Eq. omegaaprox1 (P odd) and Eq. omegaaprox2 (P even), numerators over 2(P-1)."""
+    if P == 2:
+        return [0.0, 1.0]
+    if P % 2 == 1:
+        nums = [0] + list(range(1, P - 3, 2)) + [P - 1] + list(range(P + 2, 2 * P - 2, 2)) + [2 * P - 2]
+    else:
+        nums = [0] + list(range(1, P - 4, 2)) + [P - 2, P] + list(range(P + 3, 2 * P - 2, 2)) + [2 * P - 2]
+    assert len(nums) == P
+    return [m / (2.0 * (P - 1)) for m in nums]
+
+
+def initial_guess(P, omega_1, omega_P):
+    """Initial unknowns: weights from Eqs. omegaaprox1/2 and
+    kappa_i ~ 1/omega_i + (1/omega_{i+1} - 1/omega_i)/3 (Sect. 3.5)."""
+    inv = np.array([(1.0 / omega_1) * (omega_1 / omega_P) ** e for e in guess_exponents(P)])
+    omega = 1.0 / inv
+    kint = np.array([1.0 / omega[i] + (1.0 / omega[i + 1] - 1.0 / omega[i]) / 3.0 for i in range(P - 1)])
+    return _pack(omega, kint)
+
+
+def _accept(sol, P):
+    if not np.all(np.isfinite(sol.x)) or np.max(np.abs(sol.fun)) > 1e-10:
+        return None
+    omega, kint = _unpack(sol.x, P)
+    if not np.all(np.diff(omega) < 0) or omega[-1] <= 0.5:
+        return None
+    for i in range(P - 1):
+        if not (1.0 / omega[i] < kint[i] < 1.0 / omega[i + 1]):
+            return None
+    beta = beta_theorem2(omega, kint)
+    if not np.all(beta > 0) or abs(beta.sum() - 1.0) > 1e-9:
+        return None
+    return omega, beta, kint
+
+
+def _newton(P, kappa_m, x0):
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        try:
+            sol = optimize.root(system, x0, args=(P, kappa_m), method="hybr",
+                                options=dict(xtol=1e-15, maxfev=200 * (2 * P)))
+        except (np.linalg.LinAlgError, ValueError, FloatingPointError):
+            return None
+    return _accept(sol, P)
+
+
+_GRID_R1 = (0.05, 0.1, 0.15, 0.2, 0.3, 0.35, 0.5, 0.7, 0.85, 0.95)
+_GRID_WP = (0.98, 0.95, 0.9, 0.85, 0.7, 0.6, 0.55)
+
+
+class ScheduleError(RuntimeError):
+    pass
+
+
+def solve_optimal(P, kappa_m, return_all=False):
+    """Optimal (omega, beta, kappa_int) for P levels at spectral bound kappa_m.
+
+    Levels are solved in turn from 2 to P.  For the next level the guesses of
+    omega_1 and omega_P are extrapolated from the last (up to four) solved levels
+    (quadratic fits of log omega_1 and of log(omega_P - 1/2) in P, this build's
+    reading of the conic fits of Sect. 3.3); the remaining weights follow Eqs.
+    omegaaprox1/2.  Levels with fewer than two predecessors, or whose
+    extrapolated guess fails, are started from a small grid of (omega_1,
+    omega_P) guesses and the lowest level Gamma(kappa_m) among the accepted
+    solutions is kept.
+    """
+    hist = {}
+    for p in range(2, P + 1):
+        found = None
+        if len(hist) >= 2:
+            ps = sorted(hist)[-4:]
+            deg = min(2, len(ps) - 1)
+            c1 = np.polyfit(ps, [math.log(hist[k][0][0]) for k in ps], deg)
+            cP = np.polyfit(ps, [math.log(hist[k][0][-1] - 0.5) for k in ps], deg)
+            w1 = math.exp(np.polyval(c1, p))
+            wP = 0.5 + math.exp(np.polyval(cP, p))
+            found = _newton(p, kappa_m, initial_guess(p, w1, wP))
+        if found is None:
+            best = None
+            for r1 in _GRID_R1:
+                for wP in _GRID_WP:
+                    cand = _newton(p, kappa_m, initial_guess(p, r1 / kappa_m, wP))
+                    if cand is None:
+                        continue
+                    lvl = log_gamma(kappa_m, cand[0], cand[1])[0]
+                    if best is None or lvl < best[0] - 1e-13:
+                        best = (lvl, cand)
+            found = None if best is None else best[1]
+        if found is None:
+            raise ScheduleError("no optimal SRJ scheme found for P=%d, kappa_m=%.6g" % (p, kappa_m))
+        hist[p] = found
+    return hist if return_all else hist[P]
+
+
+def polish(P, kappa_m, omega):
+    """Newton on S(omega, kappa) from given weights (e.g. a printed table row)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    kint = np.array([1.0 / omega[i] + (1.0 / omega[i + 1] - 1.0 / omega[i]) / 3.0 for i in range(P - 1)])
+    return _newton(P, kappa_m, _pack(omega, kint))
+
+
+# ---------------------------------------------------------------------------
+# Integer repetitions and validation (Sect. 4.3)
+# ---------------------------------------------------------------------------
+
+def q_floor(beta):
+    """q_i = floor(beta_i / beta_1), so q_1 = 1 (Sect. 4.3)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    return np.floor(beta / beta[0]).astype(np.int64)
+
+
+def max_cycle_factor(omega, q, kappa_m, kappa_max=KAPPA_MAX, samples=20001):
+    """max over [kappa_m, kappa_max] of log10 |cycle amplification| with integer q.
+
+    Sect. 4.3: Gamma must stay below 1 after the integer conversion, otherwise
+    SRJ diverges.  Sampled on a geometric grid plus the interior maxima of the
+    integer scheme."""
+    omega = np.asarray(omega, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    grid = np.geomspace(kappa_m, kappa_max, samples)
+    beta = q / q.sum()
+    extra = [k for k in interior_maxima(omega, beta) if kappa_m <= k <= kappa_max]
+    kap = np.concatenate([grid, extra])
+    return float(np.max(log10_cycle_factor(kap, omega, q)))
+
+
+# ---------------------------------------------------------------------------
+# Cycle ordering
+# ---------------------------------------------------------------------------
+
+def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, samples=2000):
+    """Order of the M weight applications inside one cycle.
+
+    Sect. 5.1 notes that the largest over-relaxations must be spread over the
+    cycle (an even distribution avoids overflow) but gives no algorithm.  In
+    floating point what matters is how far the partial products of the
+    amplification factors stray inside the cycle: a rounding error made at one
+    step is multiplied by the product of the factors that follow it.  This
+    ordering keeps, for every sampled kappa, the running log-product close to
+    the straight line from 0 to the full-cycle value: at step s (1-based) it
+    applies the weight, among those with repetitions left, that minimises
+      max_kappa | sum_{steps <= s} log|1-omega kappa| - (s/M) sum_i q_i log|1-omega_i kappa| |,
+    ties going to the lower level index.  kappa is sampled on a geometric grid
+    of `samples` points over [kappa_m, kappa_max].  Returns level indices
+    (0-based) of length M.
+    """
+    omega = np.asarray(omega, dtype=np.float64)
+    q = [int(v) for v in q]
+    P = len(q)
+    M = sum(q)
+    kap = np.geomspace(kappa_m, kappa_max, samples)
+    L = np.log(np.abs(1.0 - np.outer(omega, kap)))          # P x K
+    total = (np.asarray(q, float)[:, None] * L).sum(axis=0)
+    cur = np.zeros(len(kap))
+    left = list(q)
+    order = np.empty(M, dtype=np.int64)
+    for s in range(M):
+        target = total * ((s + 1) / M)
+        best_i, best_c = -1, math.inf
+        for i in range(P):
+            if left[i] == 0:
+                continue
+            c = float(np.max(np.abs(cur + L[i] - target)))
+            if c < best_c:
+                best_i, best_c = i, c
+        order[s] = best_i
+        left[best_i] -= 1
+        cur += L[best_i]
+    return order
+
+
+def window_growth(omega, order, kappa_m, kappa_max=KAPPA_MAX, samples=2000):
+    """Largest growth (log10) of any contiguous run of steps of one cycle,
+    max over kappa of max_{a<=b} |prod_{a<j<=b} (1 - omega_j kappa)|, and the
+    largest growth of any cycle suffix.  Both measure how much a rounding error
+    can be amplified inside a cycle (Sect. 5.1 overflow remark)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    kap = np.geomspace(kappa_m, kappa_max, samples)
+    L = np.log10(np.abs(1.0 - np.outer(omega, kap)))
+    pre = np.vstack([np.zeros(len(kap)), np.cumsum(L[np.asarray(order)], axis=0)])
+    window = float(np.max(pre - np.minimum.accumulate(pre, axis=0)))
+    suffix = float(np.max(pre[-1][None, :] - pre[:-1]))
+    return window, suffix
