@@ -1,0 +1,312 @@
+"""Benchmark of the SRJ hot path on GB300 (one JSON line on stdout).
+
+Workload (default): 2-D Dirichlet Poisson, 4096 x 4096 interior points, f a
+seeded N(0,1) field smoothed by a 5x5 box mean, Dirichlet data from a seeded
+cubic polynomial, optimal P = 10 SRJ schedule for this grid, FP32 sweeps inside
+FP64 defect correction, tolerance 1e-10 on the relative L2 residual.
+
+One step = one full solve from the initial guess to the tolerance (all sweeps,
+residual checks and corrections).  value = Gupdates/s = sweeps x interior
+points / step time; time-to-tolerance is reported beside it, with the plain
+FP64 SRJ on the same grid as the comparator.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl srj|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a few sweeps on the full grid) on the host cores.
+Multi-GPU (torchrun): every rank solves its own replica of the workload
+(independent problems, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 residual & Gupdates/s vs plain FP64 SRJ on same GB300; % HBM peak"
+N = 4096
+P = 10
+TOL = 1e-10
+SEED_F = 2
+MAX_CYCLES = 200
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="srj", choices=["srj", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--P", type=int, default=P)
+    ap.add_argument("--fp64-cycles", type=int, default=1,
+                    help="cycles of the plain FP64 comparator to time (0 = run it to tolerance)")
+    ap.add_argument("--cpu-sweeps", type=int, default=4, help="oracle sweeps in the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        try:
+            rows = open(self.path).read().strip().splitlines()
+        except OSError:
+            rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in rows:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if self.path:
+            os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_config(args):
+    return {"workload": "2d_poisson_%dx%d_srj_P%d_mixed_fp32_sweeps_fp64_correction" % (args.n, args.n, args.P),
+            "grid": [args.n, args.n], "stencil": "5-point", "levels_P": args.P, "tol": TOL,
+            "rhs": "seeded N(0,1) field, 5x5 box mean (seed %d); Dirichlet data: seeded cubic polynomial" % SEED_F,
+            "step": "one full solve from u0 to tolerance",
+            "l2": "flushed between timed steps (256 MiB write); per-sweep working set ~134 MB ~ L2 size"}
+
+
+def oracle_sample(args):
+    """FP64 oracle sweeps on the full grid; returns (Gupdates/s, seconds, sweeps)."""
+    import numpy as np
+    import oracle
+    import paper_1511_04292_gb300.schedules as sch
+    import srj_workloads as W
+    dims = (args.n, args.n)
+    f, u = W.random_smooth_problem_2d(args.n, SEED_F)
+    row = sch.lookup(2, args.n, args.P)
+    seq = oracle.omega_sequence(row["omega"], row["order"])
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.steps(dims, 1.0 / (args.n + 1), seq, f, u, first=0, count=args.cpu_sweeps)
+    dt = time.perf_counter() - t0
+    return args.cpu_sweeps * args.n * args.n / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    vals = []
+    for i in range(args.warmup + args.steps):
+        g, dt = oracle_sample(args)
+        if i >= args.warmup:
+            vals.append((g, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = statistics.mean(dt for _, dt in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "Gupdates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d FP64 sweeps of the full %dx%d grid per step" % (args.cpu_sweeps, args.n, args.n)},
+            "e2e": {"value": value, "unit": "Gupdates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_srj(args):
+    import numpy as np
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    n = args.n
+    dims = (n, n)
+    pts = n * n
+    f_h, u0_h = W.random_smooth_problem_2d(n, SEED_F)
+    f = torch.from_numpy(f_h).cuda()
+    u0 = torch.from_numpy(u0_h).cuda()
+    u = torch.empty_like(u0)
+    plan = srj.Plan.from_table(dims, args.P, "mixed")
+    M = plan.info()["M"]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        u.copy_(u0)
+        return plan.solve(f, u, TOL, MAX_CYCLES)
+
+    for _ in range(args.warmup):
+        st = one_solve()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            stats.append(one_solve())
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    sweeps = sum(s["sweeps"] for s in stats)
+    sweep_ms = sum(s["sweep_ms"] for s in stats)
+    if pg:
+        t = torch.tensor([total_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * sweeps * pts / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args.steps
+
+    # dominant kernel: the FP32 sweep (12 algorithmic bytes per point-update)
+    peaks, peak_kind = measured_peaks()
+    sweep_avg_ms = sweep_ms / sweeps
+    achieved = 12.0 * pts / (sweep_avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_sweep_f32<2>", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": 12 * pts,
+                "avg_launch_us": sweep_avg_ms * 1e3}
+
+    # end to end through the public API with host buffers: H2D f, u0; solve; D2H u
+    f_pin = torch.from_numpy(f_h).pin_memory()
+    u_pin = torch.from_numpy(u0_h).pin_memory()
+    out_pin = torch.empty_like(u_pin).pin_memory()
+    e2e_ms = []
+    e2e_sweeps = 0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fd = f_pin.to("cuda", non_blocking=True)
+        ud = u_pin.to("cuda", non_blocking=True)
+        st = plan.solve(fd, ud, TOL, MAX_CYCLES)
+        out_pin.copy_(ud, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        e2e_sweeps += st["sweeps"]
+    e2e_value = world * e2e_sweeps * pts / (sum(e2e_ms) / 1e3) / 1e9
+
+    # plain FP64 SRJ comparator on the same grid and schedule
+    p64 = srj.Plan.from_table(dims, args.P, "fp64")
+    u.copy_(u0)
+    torch.cuda.synchronize()
+    c64 = args.fp64_cycles if args.fp64_cycles > 0 else MAX_CYCLES
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st64 = p64.solve(f, u, TOL if args.fp64_cycles == 0 else 0.0, c64, raise_on_fail=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    g64 = st64["sweeps"] * pts / (ms64 / 1e3) / 1e9
+    cyc_mixed = stats[-1]["cycles"]
+    fp64 = {"gupdates_per_s": g64, "cycles_timed": st64["cycles"], "ms": ms64,
+            "sweep_kernel_gbs": 24.0 * pts / (st64["sweep_ms"] / st64["sweeps"] / 1e3) / 1e9,
+            "time_to_tol_s": (ms64 / 1e3 if args.fp64_cycles == 0 else ms64 / 1e3 / st64["cycles"] * cyc_mixed),
+            "time_to_tol_kind": "measured" if args.fp64_cycles == 0 else
+            "per-cycle time x the %d cycles the mixed solve needed (same cycle map in exact arithmetic)" % cyc_mixed}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, dt = oracle_sample(args)
+        cpu = {"value": g, "unit": "Gupdates/s", "cores": 1, "kind": "oracle",
+               "sample": "%d FP64 oracle sweeps of the full %dx%d grid (%.1f s)" % (args.cpu_sweeps, n, n, dt),
+               "host_cores_total": os.cpu_count()}
+
+    launches_per_step = 2 + stats[-1]["cycles"] * (M + 2)
+    line = {"metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+            "time_to_tol_s": ms_per_step / 1e3, "cycles": stats[-1]["cycles"], "sweeps_per_solve": stats[-1]["sweeps"],
+            "final_rel_residual": stats[-1]["rel_res"],
+            "fp64_comparator": fp64, "speedup_vs_fp64_time_to_tol": fp64["time_to_tol_s"] / (ms_per_step / 1e3),
+            "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "Gupdates/s", "h2d_bytes_per_step": 2 * f_h.nbytes,
+                    "d2h_bytes_per_step": u0_h.nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_srj(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

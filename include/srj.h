@@ -1,0 +1,190 @@
+/*
+ * srj.h -- C ABI of the GB300 (sm_103a) Scheduled Relaxation Jacobi library.
+ *
+ * Method: Adsuara, Cordero-Carrion, Cerda-Duran, Aloy, "Scheduled Relaxation
+ * Jacobi method: improvements and applications", arXiv:1511.04292.
+ *
+ * The library solves the Dirichlet Poisson problem -Laplace(u) = f on a uniform
+ * 2-D (5-point stencil) or 3-D (7-point stencil) grid with spacing h by SRJ:
+ * weighted-Jacobi steps (Sect. 3.1, Eq. 2nd-order_CD, with the Poisson source of
+ * Sect. 5.1)
+ *
+ *     u'_p = u_p + (omega_k / 2d) * (h^2 f_p + sum_{neighbours q} u_q - 2d u_p),
+ *
+ * whose weights omega_k run through an M-cycle in which level i (weight omega_i)
+ * appears q_i times (Sect. 2).  Convergence is tested at cycle ends on the
+ * relative L2 norm of the residual r = b - A_h u, A_h = 2d I - neighbour sum,
+ * b = h^2 f (+ Dirichlet ghost neighbours).
+ *
+ * GRID LAYOUT (all u / f / r arrays passed through this ABI)
+ *   A dense row-major float64 array of the interior points plus one ghost layer
+ *   on each side, x fastest:
+ *     2-D: element (x, y)    at  y * (nx+2) + x,                 0 <= x <= nx+1, 0 <= y <= ny+1
+ *     3-D: element (x, y, z) at  (z * (ny+2) + y) * (nx+2) + x
+ *   Interior points have 1 <= x <= nx (etc.).  The ghost layer of u carries the
+ *   Dirichlet boundary values and is never written.  The ghost layer of f is
+ *   ignored.  h is the same on every axis.
+ *
+ * POINTERS, STREAMS AND OWNERSHIP
+ *   Array arguments are DEVICE pointers on the CUDA device that was current when
+ *   the plan was created, unless a function says otherwise.  The caller owns
+ *   them; the library never frees or retains them past the call.  `stream` is a
+ *   cudaStream_t passed as void* (NULL = legacy default stream).  Work is issued
+ *   on that stream; functions that return numbers to the host (norms, stats)
+ *   synchronise with the stream before returning.  A plan owns its device
+ *   workspaces and its CUDA graphs; one plan must not be used by two host
+ *   threads at once.
+ *
+ * ERRORS
+ *   Every function returns SRJ_OK (0) or a negative status.  The text of the
+ *   last error of the calling thread is returned by srj_last_error().  After
+ *   SRJ_ERR_CUDA the CUDA context may be unusable (sticky errors).
+ */
+#ifndef SRJ_H
+#define SRJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRJ_OK                 0
+#define SRJ_ERR_INVALID_ARG   -1  /* bad dims, pointer, weight, precision ...           */
+#define SRJ_ERR_BAD_SCHEDULE  -2  /* integer scheme does not contract on the grid     */
+#define SRJ_ERR_NOT_CONVERGED -3  /* max_cycles reached before tol                   */
+#define SRJ_ERR_DIVERGED      -4  /* residual not finite, or grew by more than 1e6x   */
+#define SRJ_ERR_TIMEOUT       -5  /* a bounded device-side wait gave up               */
+#define SRJ_ERR_CUDA          -6  /* a CUDA runtime call failed                      */
+#define SRJ_ERR_NO_MEMORY     -7  /* device or host allocation failed                */
+
+/* Precision of the sweeps. */
+#define SRJ_PREC_FP64   0  /* all arithmetic in FP64; operation order fixed and
+                              without fused multiply-add, so that the iterates are
+                              reproducible bit for bit                              */
+#define SRJ_PREC_MIXED  1  /* FP64 defect correction: each M-cycle runs in FP32 on
+                              A e = r (r = b - A u in FP64, e = 0 on the boundary),
+                              then u += e in FP64                                   */
+
+typedef struct srj_plan *srj_plan_t;
+
+typedef struct srj_stats {
+    int64_t cycles;          /* M-cycles applied                                   */
+    int64_t sweeps;          /* weighted-Jacobi steps applied (= cycles * M)       */
+    int64_t residual_checks; /* residual evaluations, including the initial one   */
+    double  r0_l2;           /* ||b - A u0||_2                                     */
+    double  res_l2;          /* ||b - A u||_2 at return                            */
+    double  res_linf;        /* max_p |b - A u|_p at return                        */
+    double  rel_res;         /* res_l2 / r0_l2 (0 if r0_l2 == 0)                   */
+    double  sweep_ms;        /* device time of the M-cycle sweep graphs, summed over
+                                cycles (CUDA events on `stream`)                   */
+} srj_stats_t;
+
+/*
+ * srj_plan_create -- build an SRJ plan for one grid and one schedule.
+ *   ndim       2 or 3.
+ *   dims       interior points per axis, dims[0] = nx (fastest), dims[1] = ny
+ *              [, dims[2] = nz]; each >= 1.  Host pointer, copied.
+ *   h          mesh spacing (> 0, finite).
+ *   P          number of levels, 1 <= P <= 32.
+ *   omega      P weights omega_1..omega_P (Sect. 2; any order, each finite and
+ *              > 0).  Host pointer, copied.
+ *   q          P repetitions q_i >= 1 per cycle; M = sum q_i <= 2^20.  Host.
+ *   order      NULL, or M level indices (0-based, level i appearing exactly q_i
+ *              times) giving the order of the steps inside one cycle.  With NULL
+ *              the plan picks an order that keeps the running product of the
+ *              amplification factors near its straight-line drift (Sect. 5.1
+ *              asks only that large over-relaxations be spread out).  Host.
+ *   precision  SRJ_PREC_FP64 or SRJ_PREC_MIXED.
+ * The plan checks that the integer scheme contracts, max over kappa in
+ * [kappa_min(grid), 2] of |prod_i (1 - omega_i kappa)^q_i| < 1 (Sect. 4.3), and
+ * returns SRJ_ERR_BAD_SCHEDULE otherwise.  It allocates its workspaces on the
+ * current device: FP64 plans 3 padded float64 grids, mixed plans 3 padded
+ * float32 grids (+ a few KB).
+ */
+int srj_plan_create(srj_plan_t *plan, int ndim, const int64_t *dims, double h, int P,
+                    const double *omega, const int32_t *q, const int32_t *order, int precision);
+
+/* Free a plan and its workspaces (NULL is accepted). */
+int srj_plan_destroy(srj_plan_t plan);
+
+/*
+ * srj_plan_info -- M, the grid's kappa_min (Sect. 5.1 / Eq. boundaries1D3D:
+ * (2/d) sum_i sin^2(pi / 2(n_i+1))) and the largest log10 cycle factor found by
+ * the contraction check.  Any output pointer may be NULL.  Host pointers.
+ */
+int srj_plan_info(srj_plan_t plan, int64_t *M, double *kappa_min, double *log10_cycle_factor_max);
+
+/* srj_plan_order -- copy the M level indices of the cycle order to order_out (host). */
+int srj_plan_order(srj_plan_t plan, int32_t *order_out);
+
+/*
+ * srj_solve -- run SRJ cycles until ||r||_2 / ||r_0||_2 <= tol (checked at cycle
+ * ends) or max_cycles cycles have run.
+ *   f      device, padded layout, float64 (ghost layer ignored).
+ *   u      device, padded layout, float64: on entry the initial guess u0 with
+ *          the Dirichlet data in its ghost layer; on return the iterate.
+ *   tol    relative tolerance (>= 0).   max_cycles >= 0.
+ *   stats  host pointer or NULL.
+ * Returns SRJ_OK when converged, SRJ_ERR_NOT_CONVERGED or SRJ_ERR_DIVERGED
+ * otherwise (u then holds the last iterate and stats are filled).  Blocks the
+ * host until the solve ends; all device work is on `stream`.
+ */
+int srj_solve(srj_plan_t plan, const double *f, double *u, double tol, int64_t max_cycles,
+              void *stream, srj_stats_t *stats);
+
+/*
+ * srj_steps -- apply `count` consecutive steps of the cycle order, starting at
+ * position `first` (mod M), to u in place, without residual checks.  FP64 plans
+ * use the FP64 sweep; mixed plans round u and h^2 f to float32, apply the FP32
+ * sweep and write the float32 iterate back to u as float64.  Used to compare
+ * iterates at equal sweep counts.
+ */
+int srj_steps(srj_plan_t plan, const double *f, double *u, int64_t first, int64_t count, void *stream);
+
+/*
+ * srj_residual -- r = b - A_h u on the interior (FP64), its L2 and max norms.
+ *   r_out  device padded float64 array or NULL (ghost layer set to 0).
+ *   l2, linf  host pointers (may be NULL).
+ */
+int srj_residual(srj_plan_t plan, const double *f, const double *u, double *r_out,
+                 double *l2, double *linf, void *stream);
+
+/*
+ * srj_boundary_adjoint -- adjoint of the map from Dirichlet data g to b:
+ * for every ghost point q, grad_g[q] = sum of lambda_p over the interior
+ * neighbours p of q (b_p = h^2 f_p + sum of ghost neighbours, so dL/dg = B^T
+ * dL/db).  lambda and grad_g are device padded float64 arrays; the interior of
+ * grad_g is set to 0 and the ghost layer of lambda is ignored.
+ */
+int srj_boundary_adjoint(srj_plan_t plan, const double *lambda, double *grad_g, void *stream);
+
+/*
+ * srj_schedule_check -- host-only contraction check of an integer scheme
+ * (Sect. 4.3): *log10_max = max over kappa in [kappa_min, 2] of
+ * log10 |prod_i (1 - omega_i kappa)^q_i|; the scheme converges iff < 0.
+ * Host pointers.  Needs no GPU.
+ */
+int srj_schedule_check(int P, const double *omega, const int32_t *q, double kappa_min, double *log10_max);
+
+/*
+ * srj_schedule_order -- host-only: the cycle order srj_plan_create uses when
+ * its `order` argument is NULL (M = sum q_i level indices written to
+ * order_out).  Needs no GPU.
+ */
+int srj_schedule_order(int P, const double *omega, const int32_t *q, double kappa_min, int32_t *order_out);
+
+/* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
+int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *srj_last_error(void);
+
+/* Library version string. */
+const char *srj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRJ_H */

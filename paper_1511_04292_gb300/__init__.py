@@ -1,0 +1,136 @@
+"""GB300-native Scheduled Relaxation Jacobi (SRJ) for Dirichlet Poisson problems.
+
+Method: Adsuara, Cordero-Carrion, Cerda-Duran, Aloy, "Scheduled Relaxation
+Jacobi method: improvements and applications", arXiv:1511.04292.
+
+This module is a thin binding over the C ABI of ``include/srj.h``
+(``libsrj.so``, hand-written CUDA for sm_103a): it only marshals arguments.
+PyTorch provides device memory and streams.  Arrays are float64 CUDA tensors in
+the padded layout (nz+2, ny+2, nx+2) / (ny+2, nx+2) whose ghost layer carries
+the Dirichlet data.  There is no CPU path: without the native library every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import schedules
+from ._native import SRJError, Stats, build, check, lib
+
+__all__ = ["Plan", "SRJError", "build", "lib", "schedules", "kappa_min", "PREC_FP64", "PREC_MIXED"]
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED}
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, shape, name, writable=False):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("%s must be a float64 CUDA tensor" % name)
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be contiguous with shape %s (got %s)" % (name, tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kappa_min(dims):
+    """Smallest eigenvalue of D^-1 A for a Dirichlet grid (computed by the library)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    out = ctypes.c_double()
+    check(lib().srj_kappa_min(len(dims), d, ctypes.byref(out)))
+    return out.value
+
+
+class Plan:
+    """An SRJ plan: one grid (dims = (nx, ny[, nz]) interior points, spacing h),
+    one schedule (omega_i, q_i[, order]) and one precision ("fp64" or "mixed")."""
+
+    def __init__(self, dims, h, omega, q, order=None, precision="fp64"):
+        self.dims = tuple(int(v) for v in dims)
+        self.ndim = len(self.dims)
+        self.h = float(h)
+        self.precision = _PREC[precision]
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        qq = np.ascontiguousarray(q, dtype=np.int32)
+        od = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+        d = (ctypes.c_int64 * self.ndim)(*self.dims)
+        handle = ctypes.c_void_p()
+        self._lib = lib()
+        check(self._lib.srj_plan_create(
+            ctypes.byref(handle), self.ndim, d, self.h, len(om),
+            om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            qq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            None if od is None else od.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            self.precision))
+        self._h = handle
+        self.shape = tuple(n + 2 for n in reversed(self.dims))
+
+    @classmethod
+    def from_table(cls, dims, P, precision="fp64", h=None):
+        """Plan with the packaged schedule for an n^d grid (all dims equal)."""
+        n = int(dims[0])
+        if any(int(v) != n for v in dims):
+            raise ValueError("the packaged table covers n^d grids only")
+        row = schedules.lookup(len(dims), n, int(P))
+        return cls(dims, 1.0 / (n + 1) if h is None else h, row["omega"], row["q"], row["order"], precision)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.srj_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        M = ctypes.c_int64(); km = ctypes.c_double(); g = ctypes.c_double()
+        check(self._lib.srj_plan_info(self._h, ctypes.byref(M), ctypes.byref(km), ctypes.byref(g)))
+        return dict(M=M.value, kappa_min=km.value, log10_cycle_factor_max=g.value)
+
+    def order(self):
+        M = self.info()["M"]
+        out = np.empty(M, dtype=np.int32)
+        check(self._lib.srj_plan_order(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
+
+    def solve(self, f, u, tol, max_cycles, stream=None, raise_on_fail=True):
+        """Run SRJ cycles on u (in place) until the relative L2 residual <= tol."""
+        st = Stats()
+        rc = self._lib.srj_solve(self._h, _dev_ptr(f, self.shape, "f"), _dev_ptr(u, self.shape, "u", True),
+                                 float(tol), int(max_cycles), _stream_ptr(stream), ctypes.byref(st))
+        out = st.as_dict()
+        out["status"] = rc
+        if raise_on_fail:
+            check(rc)
+        return out
+
+    def steps(self, f, u, first=0, count=1, stream=None):
+        """Apply `count` steps of the cycle order from position `first` to u in place."""
+        check(self._lib.srj_steps(self._h, _dev_ptr(f, self.shape, "f"), _dev_ptr(u, self.shape, "u", True),
+                                  int(first), int(count), _stream_ptr(stream)))
+        return u
+
+    def residual(self, f, u, r_out=None, stream=None):
+        """(l2, linf) of r = b - A u; fills r_out (padded float64) when given."""
+        l2 = ctypes.c_double(); linf = ctypes.c_double()
+        rp = None if r_out is None else _dev_ptr(r_out, self.shape, "r_out", True)
+        check(self._lib.srj_residual(self._h, _dev_ptr(f, self.shape, "f"), _dev_ptr(u, self.shape, "u"), rp,
+                                     ctypes.byref(l2), ctypes.byref(linf), _stream_ptr(stream)))
+        return l2.value, linf.value
+
+    def boundary_adjoint(self, lam, grad_g, stream=None):
+        """grad_g[ghost] = sum of lam over interior neighbours (dL/dg from dL/db)."""
+        check(self._lib.srj_boundary_adjoint(self._h, _dev_ptr(lam, self.shape, "lam"),
+                                             _dev_ptr(grad_g, self.shape, "grad_g", True), _stream_ptr(stream)))
+        return grad_g

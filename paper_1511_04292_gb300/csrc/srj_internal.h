@@ -1,0 +1,70 @@
+// Internal declarations shared by the SRJ kernels and the host runtime.
+// Not part of the public ABI (see include/srj.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace srj {
+
+// Geometry of one grid: interior sizes, padded float64 layout (the ABI layout)
+// and the pitched float32 layout used by the mixed-precision workspaces.
+//
+// float32 layout: rows of `p32` floats (a multiple of 32, i.e. 128-byte rows);
+// padded coordinate x (0..nx+1) of a row is stored at column x + 3, so that
+// the first interior point (x = 1) sits at column 4, 16-byte aligned, and
+// float4 loads of interior points are aligned.  Rows y = 0..ny+1, planes
+// z = 0..nz+1 (3-D) follow each other densely.
+struct Geom {
+    int nd;
+    int nx, ny, nz;        // interior points (nz = 1 in 2-D)
+    int64_t sx64, sy64;    // float64 strides: row = nx+2, plane = (nx+2)(ny+2)
+    int64_t n64;           // float64 padded element count
+    int64_t p32, plane32;  // float32 row pitch (floats) and plane size
+    int64_t n32;           // float32 element count
+};
+
+Geom make_geom(int nd, const int64_t* dims);
+
+// Reduction scratch for the fused residual norms: per-block partial sums and
+// maxima, a completion counter and the final (l2, linf) pair.
+struct NormScratch {
+    double* partials;      // 2 * kMaxNormBlocks doubles
+    unsigned int* counter; // zero between launches
+    double* result;        // [0] = ||r||_2, [1] = max |r|
+};
+constexpr int kMaxNormBlocks = 1216;  // 8 blocks per SM on 152 SMs
+
+// ---- launchers (all asynchronous on `s`) ----------------------------------
+
+// b = h2 * f on the interior (float64 padded layout; ghosts of b set to 0).
+cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, double* b, cudaStream_t s);
+
+// One FP64 weighted-Jacobi step, fixed operation order, no FMA.
+//   uout = uin + c * ((sum nbrs(uin) + b) - 2d uin)    (interior only)
+cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b,
+                             double c, cudaStream_t s);
+
+// Fused residual r = (h2 * src + sum nbrs(u)) - 2d u on the interior, with L2 /
+// max norms reduced into ns.result.  Optional outputs: r64 (padded float64,
+// interior only), r32 (pitched float32, value r * scale).
+cudaError_t launch_residual(const Geom& g, const double* u, const double* src, double h2,
+                            double* r64, float* r32, double scale, NormScratch ns, cudaStream_t s);
+
+// One FP32 weighted-Jacobi step on the pitched float32 layout:
+//   eout = ein + c * ((sum nbrs(ein) + r) - 2d ein)    (interior only)
+cudaError_t launch_sweep_f32(const Geom& g, const float* ein, float* eout, const float* r,
+                             float c, cudaStream_t s);
+
+// u (float64 padded, interior) += inv_scale * e (float32 pitched).
+cudaError_t launch_update(const Geom& g, double* u, const float* e, double inv_scale, cudaStream_t s);
+
+// Layout conversions used by srj_steps on mixed plans.
+cudaError_t launch_to_f32(const Geom& g, const double* u, float* e, cudaStream_t s);          // all points
+cudaError_t launch_source_f32(const Geom& g, double h2, const double* f, float* r, cudaStream_t s);  // interior
+cudaError_t launch_from_f32(const Geom& g, const float* e, double* u, cudaStream_t s);        // interior
+
+// grad_g[ghost q] = sum of lambda over the interior neighbours of q; interior 0.
+cudaError_t launch_boundary_adjoint(const Geom& g, const double* lambda, double* grad_g, cudaStream_t s);
+
+}  // namespace srj

@@ -1,0 +1,520 @@
+// Host runtime and C ABI of the SRJ library (see include/srj.h).
+//
+// A plan holds one grid, one SRJ schedule (Sect. 2: weights omega_i repeated
+// q_i times per M-cycle) in a fixed order, its device workspaces and CUDA
+// graphs of one M-cycle of sweeps.  srj_solve replays the cycle graph and
+// checks the residual at every cycle end (Sect. 4.1 monitor, on b - A u).
+//
+// Mixed precision: each cycle runs on the defect equation A e = r in FP32
+// with e = 0 at the start and on the boundary, r = b - A u evaluated in FP64;
+// u += e in FP64 afterwards.  For a fixed cycle this is the same linear map as
+// applying the cycle to u directly (the cycle polynomial acts on the error),
+// so the convergence per cycle is that of the FP64 iteration up to FP32
+// rounding of the correction.
+#include "srj_internal.h"
+#include "../../include/srj.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define SRJ_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(SRJ_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                 \
+    } while (0)
+
+constexpr int kMaxLevels = 32;
+constexpr int64_t kMaxM = int64_t(1) << 20;
+constexpr int kOrderSamples = 2000;
+constexpr int kCheckSamples = 20001;
+
+double kappa_min_of(int nd, const int64_t* dims) {
+    const double pi = 3.14159265358979323846;
+    double s = 0.0;
+    for (int i = 0; i < nd; ++i) {
+        const double t = std::sin(pi / (2.0 * (double)(dims[i] + 1)));
+        s += t * t;
+    }
+    return (2.0 / nd) * s;
+}
+
+// log10 |cycle amplification| at kappa: sum_i q_i log10 |1 - omega_i kappa|.
+double cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, double k) {
+    double s = 0.0;
+    for (size_t i = 0; i < w.size(); ++i) s += q[i] * std::log10(std::fabs(1.0 - w[i] * k));
+    return s;
+}
+
+// Largest log10 cycle factor on [kmin, 2]: dense geometric sampling, then a
+// golden-section refinement around every sampled local maximum.
+double max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
+    const double kmax = 2.0;
+    const int n = kCheckSamples;
+    std::vector<double> ks(n), vs(n);
+    const double lr = std::log(kmax / kmin);
+    for (int i = 0; i < n; ++i) {
+        ks[i] = kmin * std::exp(lr * i / (n - 1));
+        vs[i] = cycle_log10(w, q, ks[i]);
+    }
+    ks[n - 1] = kmax;
+    vs[n - 1] = cycle_log10(w, q, kmax);
+    double best = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+        const bool lmax = (i == 0 || vs[i] >= vs[i - 1]) && (i == n - 1 || vs[i] >= vs[i + 1]);
+        if (!lmax) { best = std::max(best, vs[i]); continue; }
+        double a = ks[std::max(i - 1, 0)], b = ks[std::min(i + 1, n - 1)];
+        const double gr = 0.6180339887498949;
+        double c = b - gr * (b - a), d = a + gr * (b - a);
+        double fc = cycle_log10(w, q, c), fd = cycle_log10(w, q, d);
+        for (int it = 0; it < 80; ++it) {
+            if (fc > fd) { b = d; d = c; fd = fc; c = b - gr * (b - a); fc = cycle_log10(w, q, c); }
+            else         { a = c; c = d; fc = fd; d = a + gr * (b - a); fd = cycle_log10(w, q, d); }
+        }
+        best = std::max({best, vs[i], fc, fd});
+    }
+    return best;
+}
+
+// Cycle order that keeps, at every sampled kappa, the running log-product of
+// the amplification factors close to its straight line from 0 to the full
+// cycle value (a rounding error made at one step is multiplied by the factors
+// of the steps after it, so large excursions cost accuracy; Sect. 5.1 asks for
+// the large over-relaxations to be spread over the cycle).  Greedy: at step s
+// take the level with repetitions left that minimises the largest deviation.
+std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
+    const int P = (int)w.size();
+    const int K = kOrderSamples;
+    int64_t M = 0;
+    for (int v : q) M += v;
+    std::vector<double> L((size_t)P * K), total(K, 0.0), cur(K, 0.0);
+    const double lr = std::log(2.0 / kmin);
+    for (int j = 0; j < K; ++j) {
+        const double k = kmin * std::exp(lr * j / (K - 1));
+        for (int i = 0; i < P; ++i) {
+            L[(size_t)i * K + j] = std::log(std::fabs(1.0 - w[i] * k));
+            total[j] += q[i] * L[(size_t)i * K + j];
+        }
+    }
+    std::vector<int32_t> left(q), order((size_t)M);
+    for (int64_t s = 0; s < M; ++s) {
+        const double frac = (double)(s + 1) / (double)M;
+        int best = -1;
+        double bestc = INFINITY;
+        for (int i = 0; i < P; ++i) {
+            if (left[i] == 0) continue;
+            double c = 0.0;
+            const double* Li = &L[(size_t)i * K];
+            for (int j = 0; j < K; ++j) c = std::max(c, std::fabs(cur[j] + Li[j] - frac * total[j]));
+            if (c < bestc) { bestc = c; best = i; }
+        }
+        order[(size_t)s] = best;
+        left[best] -= 1;
+        const double* Lb = &L[(size_t)best * K];
+        for (int j = 0; j < K; ++j) cur[j] += Lb[j];
+    }
+    return order;
+}
+
+struct Stream {
+    cudaStream_t s;
+};
+
+}  // namespace
+
+struct srj_plan {
+    int device = 0;
+    srj::Geom g{};
+    int64_t dims[3] = {1, 1, 1};
+    double h = 0, h2 = 0;
+    int precision = SRJ_PREC_FP64;
+    std::vector<double> omega;
+    std::vector<int32_t> q, order;
+    int64_t M = 0;
+    std::vector<double> c64;  // omega_k / 2d per step, in cycle order
+    double kappa_min = 0, gmax = 0;
+
+    // FP64 workspaces: two iterates and b = h^2 f
+    double *ua = nullptr, *ub = nullptr, *b = nullptr;
+    // mixed workspaces: two FP32 corrections and the FP32 defect
+    float *ea = nullptr, *eb = nullptr, *r32 = nullptr;
+    srj::NormScratch ns{};
+    double* host_norms = nullptr;  // pinned, 2 doubles
+
+    cudaStream_t cap = nullptr;             // private stream used for graph capture
+    cudaGraphExec_t cycle_exec[2] = {nullptr, nullptr};  // start buffer a / b
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;            // brackets of each cycle graph
+
+    ~srj_plan() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        for (auto& ge : cycle_exec) if (ge) cudaGraphExecDestroy(ge);
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(ua); cudaFree(ub); cudaFree(b);
+        cudaFree(ea); cudaFree(eb); cudaFree(r32);
+        cudaFree(ns.partials); cudaFree(ns.counter); cudaFree(ns.result);
+        if (host_norms) cudaFreeHost(host_norms);
+    }
+};
+
+namespace {
+
+// Capture one M-cycle of sweeps starting from buffer `start` (0 = a, 1 = b).
+int capture_cycle(srj_plan* p, int start) {
+    cudaGraph_t graph = nullptr;
+    SRJ_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    if (p->precision == SRJ_PREC_FP64) {
+        for (int64_t k = 0; k < p->M && err == cudaSuccess; ++k) {
+            const bool from_a = ((k + start) % 2) == 0;
+            err = srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
+                                        p->c64[(size_t)k], p->cap);
+        }
+    } else {
+        err = cudaMemsetAsync(p->ea, 0, sizeof(float) * (size_t)p->g.n32, p->cap);
+        for (int64_t k = 0; k < p->M && err == cudaSuccess; ++k) {
+            const bool from_a = (k % 2) == 0;
+            err = srj::launch_sweep_f32(p->g, from_a ? p->ea : p->eb, from_a ? p->eb : p->ea, p->r32,
+                                        (float)p->c64[(size_t)k], p->cap);
+        }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SRJ_CUDA(err); }
+    SRJ_CUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&p->cycle_exec[start], graph, 0);
+    cudaGraphDestroy(graph);
+    SRJ_CUDA(e3);
+    return SRJ_OK;
+}
+
+int check_plan(srj_plan_t p) {
+    if (!p) return fail(SRJ_ERR_INVALID_ARG, "plan is NULL");
+    int dev = -1;
+    SRJ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(SRJ_ERR_INVALID_ARG, "plan was created on device %d, current is %d", p->device, dev);
+    return SRJ_OK;
+}
+
+int read_norms(srj_plan* p, cudaStream_t s, double* l2, double* linf) {
+    SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    *l2 = p->host_norms[0];
+    *linf = p->host_norms[1];
+    return SRJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* srj_last_error(void) { return g_last_error.c_str(); }
+
+const char* srj_version(void) { return "srj-gb300 0.1 (sm_103a)"; }
+
+int srj_kappa_min(int ndim, const int64_t* dims, double* kappa_min) {
+    if ((ndim != 2 && ndim != 3) || !dims || !kappa_min) return fail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < ndim; ++i) if (dims[i] < 1) return fail(SRJ_ERR_INVALID_ARG, "dims must be >= 1");
+    *kappa_min = kappa_min_of(ndim, dims);
+    return SRJ_OK;
+}
+
+static int check_levels(int P, const double* omega, const int32_t* q, int64_t* M) {
+    if (P < 1 || P > kMaxLevels) return fail(SRJ_ERR_INVALID_ARG, "P must be in 1..%d", kMaxLevels);
+    if (!omega || !q) return fail(SRJ_ERR_INVALID_ARG, "omega and q must be non-NULL");
+    *M = 0;
+    for (int i = 0; i < P; ++i) {
+        if (!(omega[i] > 0.0) || !std::isfinite(omega[i])) return fail(SRJ_ERR_INVALID_ARG, "omega[%d] must be finite and > 0", i);
+        if (q[i] < 1) return fail(SRJ_ERR_INVALID_ARG, "q[%d] must be >= 1", i);
+        *M += q[i];
+    }
+    if (*M > kMaxM) return fail(SRJ_ERR_INVALID_ARG, "M = %lld exceeds %lld", (long long)*M, (long long)kMaxM);
+    return SRJ_OK;
+}
+
+int srj_schedule_check(int P, const double* omega, const int32_t* q, double kappa_min, double* log10_max) {
+    int64_t M = 0;
+    int rc = check_levels(P, omega, q, &M);
+    if (rc) return rc;
+    if (!log10_max || !(kappa_min > 0.0) || !(kappa_min < 2.0)) return fail(SRJ_ERR_INVALID_ARG, "bad kappa_min or output");
+    *log10_max = max_cycle_log10(std::vector<double>(omega, omega + P), std::vector<int32_t>(q, q + P), kappa_min);
+    return SRJ_OK;
+}
+
+int srj_schedule_order(int P, const double* omega, const int32_t* q, double kappa_min, int32_t* order_out) {
+    int64_t M = 0;
+    int rc = check_levels(P, omega, q, &M);
+    if (rc) return rc;
+    if (!order_out || !(kappa_min > 0.0) || !(kappa_min < 2.0)) return fail(SRJ_ERR_INVALID_ARG, "bad kappa_min or output");
+    std::vector<int32_t> o = drift_order(std::vector<double>(omega, omega + P), std::vector<int32_t>(q, q + P), kappa_min);
+    std::memcpy(order_out, o.data(), sizeof(int32_t) * o.size());
+    return SRJ_OK;
+}
+
+int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, int P, const double* omega,
+                    const int32_t* q, const int32_t* order, int precision) {
+    if (!out) return fail(SRJ_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(SRJ_ERR_INVALID_ARG, "ndim must be 2 or 3 (got %d)", ndim);
+    if (!dims || !omega || !q) return fail(SRJ_ERR_INVALID_ARG, "dims, omega and q must be non-NULL");
+    for (int i = 0; i < ndim; ++i)
+        if (dims[i] < 1 || dims[i] > (int64_t(1) << 30))
+            return fail(SRJ_ERR_INVALID_ARG, "dims[%d] = %lld out of range", i, (long long)dims[i]);
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(SRJ_ERR_INVALID_ARG, "h must be finite and > 0");
+    if (precision != SRJ_PREC_FP64 && precision != SRJ_PREC_MIXED)
+        return fail(SRJ_ERR_INVALID_ARG, "unknown precision %d", precision);
+    int64_t M = 0;
+    if (int rc0 = check_levels(P, omega, q, &M)) return rc0;
+    if (dims[1] > 262140) return fail(SRJ_ERR_INVALID_ARG, "dims[1] must be <= 262140 (launch grid limit)");
+    const int64_t pts = dims[0] * dims[1] * (ndim == 3 ? dims[2] : 1);
+    if (pts > (int64_t(1) << 36)) return fail(SRJ_ERR_INVALID_ARG, "grid too large");
+
+    srj_plan* p = new (std::nothrow) srj_plan();
+    if (!p) return fail(SRJ_ERR_NO_MEMORY, "host allocation failed");
+    auto bail = [&](int code) { delete p; return code; };
+
+    p->omega.assign(omega, omega + P);
+    p->q.assign(q, q + P);
+    p->M = M;
+    p->precision = precision;
+    p->h = h;
+    p->h2 = h * h;
+    for (int i = 0; i < ndim; ++i) p->dims[i] = dims[i];
+    p->g = srj::make_geom(ndim, dims);
+    p->kappa_min = kappa_min_of(ndim, dims);
+
+    p->gmax = max_cycle_log10(p->omega, p->q, p->kappa_min);
+    if (!(p->gmax < 0.0))
+        return bail(fail(SRJ_ERR_BAD_SCHEDULE,
+                         "integer scheme does not contract on [kappa_min=%.6g, 2]: max log10 cycle factor %.4g",
+                         p->kappa_min, p->gmax));
+
+    if (order) {
+        std::vector<int64_t> cnt(P, 0);
+        for (int64_t k = 0; k < M; ++k) {
+            if (order[k] < 0 || order[k] >= P) return bail(fail(SRJ_ERR_INVALID_ARG, "order[%lld] out of range", (long long)k));
+            cnt[order[k]]++;
+        }
+        for (int i = 0; i < P; ++i)
+            if (cnt[i] != q[i]) return bail(fail(SRJ_ERR_INVALID_ARG, "order uses level %d %lld times, q=%d", i, (long long)cnt[i], q[i]));
+        p->order.assign(order, order + M);
+    } else {
+        p->order = drift_order(p->omega, p->q, p->kappa_min);
+    }
+    p->c64.resize((size_t)M);
+    for (int64_t k = 0; k < M; ++k) p->c64[(size_t)k] = p->omega[p->order[(size_t)k]] / (double)(2 * ndim);
+
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(SRJ_ERR_CUDA, "no CUDA device"));
+    auto alloc = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes) == cudaSuccess; };
+    bool ok = true;
+    if (precision == SRJ_PREC_FP64) {
+        const size_t by = sizeof(double) * (size_t)p->g.n64;
+        ok = alloc((void**)&p->ua, by) && alloc((void**)&p->ub, by) && alloc((void**)&p->b, by);
+    } else {
+        const size_t by = sizeof(float) * (size_t)p->g.n32;
+        ok = alloc((void**)&p->ea, by) && alloc((void**)&p->eb, by) && alloc((void**)&p->r32, by);
+        if (ok) ok = cudaMemset(p->ea, 0, by) == cudaSuccess && cudaMemset(p->eb, 0, by) == cudaSuccess &&
+                     cudaMemset(p->r32, 0, by) == cudaSuccess;
+    }
+    ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 2 * srj::kMaxNormBlocks) &&
+         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double));
+    if (!ok) { cudaGetLastError(); return bail(fail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
+    if (cudaMemset(p->ns.counter, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->host_norms, 2 * sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SRJ_ERR_CUDA, "plan setup failed"));
+    }
+    int rc = capture_cycle(p, 0);
+    if (rc == SRJ_OK && precision == SRJ_PREC_FP64 && (M % 2) == 1) rc = capture_cycle(p, 1);
+    if (rc != SRJ_OK) return bail(rc);
+    if (cudaStreamSynchronize(p->cap) != cudaSuccess) return bail(fail(SRJ_ERR_CUDA, "plan setup sync failed"));
+    *out = p;
+    return SRJ_OK;
+}
+
+int srj_plan_destroy(srj_plan_t plan) {
+    if (!plan) return SRJ_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != plan->device) cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    delete plan;
+    if (dev >= 0 && dev != plan->device) cudaSetDevice(dev);
+    return SRJ_OK;
+}
+
+int srj_plan_info(srj_plan_t plan, int64_t* M, double* kappa_min, double* gmax) {
+    if (!plan) return fail(SRJ_ERR_INVALID_ARG, "plan is NULL");
+    if (M) *M = plan->M;
+    if (kappa_min) *kappa_min = plan->kappa_min;
+    if (gmax) *gmax = plan->gmax;
+    return SRJ_OK;
+}
+
+int srj_plan_order(srj_plan_t plan, int32_t* out) {
+    if (!plan || !out) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    std::memcpy(out, plan->order.data(), sizeof(int32_t) * (size_t)plan->M);
+    return SRJ_OK;
+}
+
+int srj_residual(srj_plan_t p, const double* f, const double* u, double* r_out, double* l2, double* linf,
+                 void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r_out) SRJ_CUDA(cudaMemsetAsync(r_out, 0, sizeof(double) * (size_t)p->g.n64, s));
+    SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, r_out, nullptr, 1.0, p->ns, s));
+    double a, bb;
+    rc = read_norms(p, s, &a, &bb);
+    if (rc) return rc;
+    if (l2) *l2 = a;
+    if (linf) *linf = bb;
+    return SRJ_OK;
+}
+
+int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t count, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!f || !u || count < 0) return fail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t M = p->M;
+    first = ((first % M) + M) % M;
+    if (p->precision == SRJ_PREC_FP64) {
+        const size_t by = sizeof(double) * (size_t)p->g.n64;
+        SRJ_CUDA(cudaMemcpyAsync(p->ua, u, by, cudaMemcpyDeviceToDevice, s));
+        SRJ_CUDA(cudaMemcpyAsync(p->ub, u, by, cudaMemcpyDeviceToDevice, s));
+        SRJ_CUDA(srj::launch_scale_source(p->g, p->h2, f, p->b, s));
+        for (int64_t k = 0; k < count; ++k) {
+            const bool from_a = (k % 2) == 0;
+            SRJ_CUDA(srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
+                                           p->c64[(size_t)((first + k) % M)], s));
+        }
+        SRJ_CUDA(cudaMemcpyAsync(u, (count % 2) ? p->ub : p->ua, by, cudaMemcpyDeviceToDevice, s));
+    } else {
+        SRJ_CUDA(srj::launch_to_f32(p->g, u, p->ea, s));
+        SRJ_CUDA(srj::launch_to_f32(p->g, u, p->eb, s));
+        SRJ_CUDA(cudaMemsetAsync(p->r32, 0, sizeof(float) * (size_t)p->g.n32, s));
+        SRJ_CUDA(srj::launch_source_f32(p->g, p->h2, f, p->r32, s));
+        for (int64_t k = 0; k < count; ++k) {
+            const bool from_a = (k % 2) == 0;
+            SRJ_CUDA(srj::launch_sweep_f32(p->g, from_a ? p->ea : p->eb, from_a ? p->eb : p->ea, p->r32,
+                                           (float)p->c64[(size_t)((first + k) % M)], s));
+        }
+        SRJ_CUDA(srj::launch_from_f32(p->g, (count % 2) ? p->eb : p->ea, u, s));
+    }
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return SRJ_OK;
+}
+
+int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_cycles, void* stream,
+              srj_stats_t* stats) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
+    if (!(tol >= 0.0) || max_cycles < 0) return fail(SRJ_ERR_INVALID_ARG, "tol must be >= 0 and max_cycles >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    srj_stats_t st{};
+    const size_t by64 = sizeof(double) * (size_t)p->g.n64;
+    double l2 = 0, linf = 0;
+    int cur = 0;  // FP64: which buffer holds the iterate (0 = ua, 1 = ub)
+    double scale = 1.0;
+
+    if (p->precision == SRJ_PREC_FP64) {
+        SRJ_CUDA(cudaMemcpyAsync(p->ua, u, by64, cudaMemcpyDeviceToDevice, s));
+        SRJ_CUDA(cudaMemcpyAsync(p->ub, u, by64, cudaMemcpyDeviceToDevice, s));
+        SRJ_CUDA(srj::launch_scale_source(p->g, p->h2, f, p->b, s));
+        SRJ_CUDA(srj::launch_residual(p->g, p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s));
+    } else {
+        const size_t by32 = sizeof(float) * (size_t)p->g.n32;
+        SRJ_CUDA(cudaMemsetAsync(p->eb, 0, by32, s));  // ghosts of the corrections are 0
+        SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, nullptr, 1.0, p->ns, s));
+    }
+    if ((rc = read_norms(p, s, &l2, &linf))) return rc;
+    st.residual_checks = 1;
+    st.r0_l2 = l2;
+    st.res_l2 = l2;
+    st.res_linf = linf;
+    st.rel_res = l2 > 0 ? 1.0 : 0.0;
+    int status = SRJ_OK;
+    if (!std::isfinite(l2)) status = fail(SRJ_ERR_DIVERGED, "initial residual is not finite");
+    else if (l2 > 0.0 && !(1.0 <= tol)) {
+        status = SRJ_ERR_NOT_CONVERGED;
+        if (p->precision == SRJ_PREC_MIXED) {
+            // FP32 defect scaled by a power of two so that its largest entry is ~1
+            int ex = 0;
+            std::frexp(linf, &ex);
+            scale = std::ldexp(1.0, -ex);
+            SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, p->r32, scale, p->ns, s));
+        }
+        for (int64_t c = 0; c < max_cycles; ++c) {
+            SRJ_CUDA(cudaEventRecord(p->ev0, s));
+            if (p->precision == SRJ_PREC_FP64) {
+                SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[p->M % 2 ? cur : 0], s));
+                SRJ_CUDA(cudaEventRecord(p->ev1, s));
+                if (p->M % 2) cur ^= 1;
+                SRJ_CUDA(srj::launch_residual(p->g, cur ? p->ub : p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s));
+            } else {
+                SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[0], s));
+                SRJ_CUDA(cudaEventRecord(p->ev1, s));
+                SRJ_CUDA(srj::launch_update(p->g, u, (p->M % 2) ? p->eb : p->ea, 1.0 / scale, s));
+                SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, p->r32, scale, p->ns, s));
+            }
+            if ((rc = read_norms(p, s, &l2, &linf))) return rc;
+            float ms = 0.f;
+            SRJ_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+            st.sweep_ms += ms;
+            st.cycles = c + 1;
+            st.sweeps = st.cycles * p->M;
+            st.residual_checks += 1;
+            st.res_l2 = l2;
+            st.res_linf = linf;
+            st.rel_res = l2 / st.r0_l2;
+            if (!std::isfinite(l2) || l2 > 1e6 * st.r0_l2) {
+                status = fail(SRJ_ERR_DIVERGED, "residual diverged at cycle %lld (rel %.3g)", (long long)(c + 1), st.rel_res);
+                break;
+            }
+            if (st.rel_res <= tol) { status = SRJ_OK; break; }
+        }
+        if (status == SRJ_ERR_NOT_CONVERGED)
+            fail(SRJ_ERR_NOT_CONVERGED, "not converged after %lld cycles (rel %.3g)", (long long)max_cycles, st.rel_res);
+    }
+    if (p->precision == SRJ_PREC_FP64 && st.cycles > 0)
+        SRJ_CUDA(cudaMemcpyAsync(u, cur ? p->ub : p->ua, by64, cudaMemcpyDeviceToDevice, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    if (stats) *stats = st;
+    return status;
+}
+
+int srj_boundary_adjoint(srj_plan_t p, const double* lambda, double* grad_g, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!lambda || !grad_g) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    SRJ_CUDA(srj::launch_boundary_adjoint(p->g, lambda, grad_g, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return SRJ_OK;
+}
+
+}  // extern "C"

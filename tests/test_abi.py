@@ -1,0 +1,114 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol that
+include/srj.h declares, and its host-only logic (argument checks, spectral
+bound, contraction check, cycle order) behaves as specified."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1511_04292_gb300 as srj
+from oracle import schedule as S
+
+HEADER = Path(__file__).resolve().parent.parent / "include" / "srj.h"
+
+
+def declared_functions():
+    text = re.sub(r"/\*.*?\*/", "", HEADER.read_text(), flags=re.S)
+    return sorted(set(re.findall(r"\b(srj_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = srj.lib()
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(srj._native.SIGNATURES), "binding and header disagree"
+
+
+def test_kappa_min_matches_oracle():
+    for dims in [(128, 128), (585 - 1, 280 - 1), (512, 512, 512), (7, 3, 5)]:
+        assert abs(srj.kappa_min(dims) / oracle.kappa_min_dirichlet(dims) - 1) < 1e-14
+
+
+def _arr(a, t):
+    return np.ascontiguousarray(a, dtype=t)
+
+
+def test_schedule_check_agrees_with_oracle():
+    L = srj.lib()
+    for n, P in [(128, 5), (4096, 10), (512, 12)]:
+        nd = 3 if (n, P) == (512, 12) else 2
+        row = srj.schedules.lookup(nd, n, P)
+        w, q = _arr(row["omega"], np.float64), _arr(row["q"], np.int32)
+        out = ctypes.c_double()
+        srj._native.check(L.srj_schedule_check(P, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                               row["kappa_min"], ctypes.byref(out)))
+        ref = S.max_cycle_factor(row["omega"], row["q"], row["kappa_min"])
+        assert out.value < 0 and abs(out.value - ref) < 1e-6 * max(1.0, abs(ref)), (out.value, ref)
+
+
+def test_plan_rejects_non_contracting_scheme_before_touching_the_gpu():
+    w = _arr([100.0, 0.6], np.float64)
+    q = _arr([50, 1], np.int32)  # far too many large steps
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 2)(64, 64)
+    rc = srj.lib().srj_plan_create(ctypes.byref(h), 2, d, 1 / 65, 2,
+                                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, 0)
+    assert rc == -2 and not h.value
+    assert b"does not contract" in srj.lib().srj_last_error()
+
+
+@pytest.mark.parametrize("bad", ["ndim", "dims", "h", "P", "omega", "q", "order", "precision"])
+def test_plan_argument_checks(bad):
+    w = _arr([2.0, 0.7], np.float64)
+    q = _arr([1, 3], np.int32)
+    order = _arr([1, 0, 1, 1], np.int32)
+    args = dict(ndim=2, dims=(ctypes.c_int64 * 2)(8, 8), h=0.1, P=2, omega=w, q=q, order=order, precision=0)
+    if bad == "ndim": args["ndim"] = 4
+    if bad == "dims": args["dims"] = (ctypes.c_int64 * 2)(0, 8)
+    if bad == "h": args["h"] = -1.0
+    if bad == "P": args["P"] = 0
+    if bad == "omega": args["omega"] = _arr([2.0, float("nan")], np.float64)
+    if bad == "q": args["q"] = _arr([1, 0], np.int32)
+    if bad == "order": args["order"] = _arr([1, 1, 1, 1], np.int32)
+    if bad == "precision": args["precision"] = 7
+    h = ctypes.c_void_p()
+    rc = srj.lib().srj_plan_create(ctypes.byref(h), args["ndim"], args["dims"], args["h"], args["P"],
+                                   args["omega"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   args["q"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   args["order"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   args["precision"])
+    assert rc == -1, (bad, rc)
+
+
+@pytest.mark.parametrize("n,P", [(128, 5), (4096, 10)])
+def test_library_order_has_bounded_window_growth(n, P):
+    """The plan's own cycle order (used when none is given) is a valid cycle and
+    keeps the worst in-cycle growth within one decade of |1 - 2 omega_1|, like the
+    oracle-side order (independent implementations of the same rule)."""
+    row = srj.schedules.lookup(2, n, P)
+    w, q = _arr(row["omega"], np.float64), _arr(row["q"], np.int32)
+    out = np.empty(int(q.sum()), dtype=np.int32)
+    srj._native.check(srj.lib().srj_schedule_order(P, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                   q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                   row["kappa_min"], out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    assert np.bincount(out, minlength=P).tolist() == q.tolist()
+    window, suffix = S.window_growth(row["omega"], out, row["kappa_min"])
+    floor = np.log10(2 * row["omega"][0] - 1)
+    assert window <= floor + 1.0 and suffix <= floor
+
+
+def test_packaged_schedules_contract_and_match_their_order():
+    """Every packaged row: integer scheme contracts (Sect. 4.3) and its order
+    string lists each level exactly q_i times."""
+    for nd, n, P in srj.schedules.available():
+        row = srj.schedules.lookup(nd, n, P)
+        assert row["log10_cycle_factor_max"] < 0
+        assert np.bincount(row["order"], minlength=P).tolist() == row["q"].tolist()
+        assert abs(row["kappa_min"] - oracle.kappa_min_dirichlet([n] * nd)) < 1e-15
