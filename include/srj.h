@@ -96,9 +96,11 @@ typedef struct srj_stats {
  *              amplification factors near its straight-line drift (Sect. 5.1
  *              asks only that large over-relaxations be spread out).  Host.
  *   precision  SRJ_PREC_FP64 or SRJ_PREC_MIXED.
- * The plan checks that the integer scheme contracts, max over kappa in
- * [kappa_min(grid), 2] of |prod_i (1 - omega_i kappa)^q_i| < 1 (Sect. 4.3), and
- * returns SRJ_ERR_BAD_SCHEDULE otherwise.  It allocates its workspaces on the
+ * The plan checks that the integer scheme contracts on the grid's spectrum,
+ * max over kappa in [kappa_min, kappa_max] of |prod_i (1 - omega_i kappa)^q_i| < 1
+ * (Sect. 4.3), with kappa_min = (2/d) sum_i sin^2(pi / 2(n_i+1)) and
+ * kappa_max = (2/d) sum_i cos^2(pi / 2(n_i+1)) < 2 the extreme eigenvalues of
+ * D^-1 A_h, and returns SRJ_ERR_BAD_SCHEDULE otherwise.  It allocates its workspaces on the
  * current device: FP64 plans 3 padded float64 grids, mixed plans 3 padded
  * float32 grids (+ a few KB).
  */
@@ -161,11 +163,13 @@ int srj_boundary_adjoint(srj_plan_t plan, const double *lambda, double *grad_g, 
 
 /*
  * srj_schedule_check -- host-only contraction check of an integer scheme
- * (Sect. 4.3): *log10_max = max over kappa in [kappa_min, 2] of
+ * (Sect. 4.3): *log10_max = max over kappa in [kappa_min, kappa_max] of
  * log10 |prod_i (1 - omega_i kappa)^q_i|; the scheme converges iff < 0.
- * Host pointers.  Needs no GPU.
+ * 0 < kappa_min < kappa_max <= 2 (Eq. boundaries: kappa_M = 2 bounds every
+ * grid).  Host pointers.  Needs no GPU.
  */
-int srj_schedule_check(int P, const double *omega, const int32_t *q, double kappa_min, double *log10_max);
+int srj_schedule_check(int P, const double *omega, const int32_t *q, double kappa_min, double kappa_max,
+                       double *log10_max);
 
 /*
  * srj_schedule_order -- host-only: the cycle order srj_plan_create uses when

@@ -100,7 +100,7 @@ SIGNATURES = {
     "srj_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),
     "srj_boundary_adjoint": (_I, [_VP, _VP, _VP, _VP]),
     "srj_kappa_min": (_I, [_I, _I64P, _DP]),
-    "srj_schedule_check": (_I, [_I, _DP, _I32P, _D, _DP]),
+    "srj_schedule_check": (_I, [_I, _DP, _I32P, _D, _D, _DP]),
     "srj_schedule_order": (_I, [_I, _DP, _I32P, _D, _I32P]),
     "srj_last_error": (ctypes.c_char_p, []),
     "srj_version": (ctypes.c_char_p, []),

@@ -49,6 +49,17 @@ constexpr int64_t kMaxM = int64_t(1) << 20;
 constexpr int kOrderSamples = 2000;
 constexpr int kCheckSamples = 20001;
 
+// Largest eigenvalue of D^-1 A on the Dirichlet grid: (2/d) sum_i cos^2(pi / 2(n_i+1)) < 2.
+double kappa_max_of(int nd, const int64_t* dims) {
+    const double pi = 3.14159265358979323846;
+    double s = 0.0;
+    for (int i = 0; i < nd; ++i) {
+        const double t = std::cos(pi / (2.0 * (double)(dims[i] + 1)));
+        s += t * t;
+    }
+    return (2.0 / nd) * s;
+}
+
 double kappa_min_of(int nd, const int64_t* dims) {
     const double pi = 3.14159265358979323846;
     double s = 0.0;
@@ -66,10 +77,9 @@ double cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, 
     return s;
 }
 
-// Largest log10 cycle factor on [kmin, 2]: dense geometric sampling, then a
+// Largest log10 cycle factor on [kmin, kmax]: dense geometric sampling, then a
 // golden-section refinement around every sampled local maximum.
-double max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
-    const double kmax = 2.0;
+double max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin, double kmax) {
     const int n = kCheckSamples;
     std::vector<double> ks(n), vs(n);
     const double lr = std::log(kmax / kmin);
@@ -152,7 +162,7 @@ struct srj_plan {
     std::vector<int32_t> q, order;
     int64_t M = 0;
     std::vector<double> c64;  // omega_k / 2d per step, in cycle order
-    double kappa_min = 0, gmax = 0;
+    double kappa_min = 0, kappa_max = 2, gmax = 0;
 
     // FP64 workspaces: two iterates and b = h^2 f
     double *ua = nullptr, *ub = nullptr, *b = nullptr;
@@ -251,12 +261,15 @@ static int check_levels(int P, const double* omega, const int32_t* q, int64_t* M
     return SRJ_OK;
 }
 
-int srj_schedule_check(int P, const double* omega, const int32_t* q, double kappa_min, double* log10_max) {
+int srj_schedule_check(int P, const double* omega, const int32_t* q, double kappa_min, double kappa_max,
+                       double* log10_max) {
     int64_t M = 0;
     int rc = check_levels(P, omega, q, &M);
     if (rc) return rc;
-    if (!log10_max || !(kappa_min > 0.0) || !(kappa_min < 2.0)) return fail(SRJ_ERR_INVALID_ARG, "bad kappa_min or output");
-    *log10_max = max_cycle_log10(std::vector<double>(omega, omega + P), std::vector<int32_t>(q, q + P), kappa_min);
+    if (!log10_max || !(kappa_min > 0.0) || !(kappa_min < kappa_max) || !(kappa_max <= 2.0))
+        return fail(SRJ_ERR_INVALID_ARG, "need 0 < kappa_min < kappa_max <= 2 and an output pointer");
+    *log10_max = max_cycle_log10(std::vector<double>(omega, omega + P), std::vector<int32_t>(q, q + P), kappa_min,
+                                 kappa_max);
     return SRJ_OK;
 }
 
@@ -301,12 +314,14 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
     for (int i = 0; i < ndim; ++i) p->dims[i] = dims[i];
     p->g = srj::make_geom(ndim, dims);
     p->kappa_min = kappa_min_of(ndim, dims);
+    p->kappa_max = kappa_max_of(ndim, dims);
 
-    p->gmax = max_cycle_log10(p->omega, p->q, p->kappa_min);
+    p->gmax = p->kappa_min < p->kappa_max ? max_cycle_log10(p->omega, p->q, p->kappa_min, p->kappa_max)
+                                          : cycle_log10(p->omega, p->q, p->kappa_min);
     if (!(p->gmax < 0.0))
         return bail(fail(SRJ_ERR_BAD_SCHEDULE,
-                         "integer scheme does not contract on [kappa_min=%.6g, 2]: max log10 cycle factor %.4g",
-                         p->kappa_min, p->gmax));
+                         "integer scheme does not contract on [kappa_min=%.6g, kappa_max=%.6g]: max log10 cycle factor %.4g",
+                         p->kappa_min, p->kappa_max, p->gmax));
 
     if (order) {
         std::vector<int64_t> cnt(P, 0);

@@ -47,7 +47,7 @@ def test_schedule_check_agrees_with_oracle():
         out = ctypes.c_double()
         srj._native.check(L.srj_schedule_check(P, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                               row["kappa_min"], ctypes.byref(out)))
+                                               row["kappa_min"], 2.0, ctypes.byref(out)))
         ref = S.max_cycle_factor(row["omega"], row["q"], row["kappa_min"])
         assert out.value < 0 and abs(out.value - ref) < 1e-6 * max(1.0, abs(ref)), (out.value, ref)
 
