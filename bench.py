@@ -51,7 +51,26 @@ def parse():
                     help="cycles of the plain FP64 comparator to time (0 = run it to tolerance)")
     ap.add_argument("--cpu-sweeps", type=int, default=4, help="oracle sweeps in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", choices=["f32", "f64"], default=None,
+                    help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
+                         "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
+    ap.add_argument("--count", type=int, default=4)
     return ap.parse_args()
+
+
+def run_kernel_case(args):
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
+    n = args.n
+    torch.cuda.set_device(0)
+    plan = srj.Plan((n, n), 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
+    f = torch.from_numpy(W.random_field((n, n), 1)).cuda()
+    u = torch.from_numpy(W.random_field((n, n), 2)).cuda()
+    plan.steps(f, u, 0, args.count)
+    torch.cuda.synchronize()
+    print("kernel case %s n=%d count=%d done" % (args.kernel_case, n, args.count))
+    return 0
 
 
 def dist_info():
@@ -303,6 +322,8 @@ def run_srj(args):
 
 def main():
     args = parse()
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_srj(args)
