@@ -181,6 +181,38 @@ int srj_schedule_order(int P, const double *omega, const int32_t *q, double kapp
 /* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 
+/*
+ * srj_steps_f32_noalloc -- the FP32 sweep of srj_steps without any device
+ * allocation.  (The paper has no counterpart: this is a library service.)
+ *
+ * For callers that cannot allocate device memory when they need a few sweeps:
+ * code whose device memory is all owned by its own fixed pool, latency-critical
+ * loops in which cudaMalloc / cudaFree would synchronise the device, and code
+ * running while a stream is being captured.  Instead of a plan's workspaces the
+ * work buffers live in one static device array of 12 MiB (3 x 2^20 floats) that
+ * every GPU loading this library holds until the process exits; grids whose
+ * pitched float32 layout needs more than 2^20 floats per buffer (about 1M padded
+ * points, e.g. 1016 x 1016 or 96^3) are rejected with SRJ_ERR_INVALID_ARG.
+ *
+ * Applies `count` FP32 weighted-Jacobi steps with weights omega_seq[0..count-1]
+ * (host array) to u in place, exactly as srj_steps does on a mixed-precision plan
+ * whose cycle order gives the same weights: u and h^2 f are rounded to float32,
+ * the sweeps run in float32, the interior of u is written back as float64 and its
+ * ghost layer is left untouched.  f, u: device arrays in the padded layout.
+ * Blocks until the work on `stream` is done.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls share the array, which keeps the last call's contents (each call clears
+ * what it reads); calls whose GPU work overlaps race on it.  Errors are
+ * reported through srj_noalloc_last_error().
+ */
+int srj_steps_f32_noalloc(int ndim, const int64_t *dims, double h, int64_t count, const double *omega_seq,
+                          const double *f, double *u, void *stream);
+
+/* Text of the last error of srj_steps_f32_noalloc on the calling thread. */
+const char *srj_noalloc_last_error(void);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char *srj_last_error(void);
 
