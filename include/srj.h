@@ -117,6 +117,27 @@ int srj_plan_destroy(srj_plan_t plan);
  */
 int srj_plan_info(srj_plan_t plan, int64_t *M, double *kappa_min, double *log10_cycle_factor_max);
 
+/*
+ * srj_plan_set_temporal_depth -- number T (1..8) of consecutive FP32 steps that
+ * one sweep launch applies to a tile held in shared memory (temporal blocking;
+ * T = 1 is the plain one-step sweep).  Available for 2-D mixed-precision plans
+ * (default 4); every other plan accepts only T = 1.  T blocked steps give the
+ * same bits as T single steps.  Re-captures the plan's cycle graph.
+ */
+int srj_plan_set_temporal_depth(srj_plan_t plan, int T);
+
+/* srj_plan_temporal_depth -- current temporal depth (host output). */
+int srj_plan_temporal_depth(srj_plan_t plan, int *T);
+
+/*
+ * srj_plan_autotune -- time the plan's sweep for every admissible temporal depth
+ * on its own workspaces (a few hundred steps each, CUDA events on `stream`),
+ * keep the fastest and report it (best_T, microseconds per step; either output
+ * may be NULL).  The workspaces' contents are overwritten; srj_solve resets
+ * them.  Blocks until done.
+ */
+int srj_plan_autotune(srj_plan_t plan, void *stream, int *best_T, float *best_us_per_step);
+
 /* srj_plan_order -- copy the M level indices of the cycle order to order_out (host). */
 int srj_plan_order(srj_plan_t plan, int32_t *order_out);
 

@@ -98,6 +98,21 @@ class Plan:
         check(self._lib.srj_plan_info(self._h, ctypes.byref(M), ctypes.byref(km), ctypes.byref(g)))
         return dict(M=M.value, kappa_min=km.value, log10_cycle_factor_max=g.value)
 
+    def set_temporal_depth(self, T):
+        """Steps per blocked FP32 sweep launch (1 = unblocked); 2-D mixed plans only."""
+        check(self._lib.srj_plan_set_temporal_depth(self._h, int(T)))
+
+    def temporal_depth(self):
+        T = ctypes.c_int()
+        check(self._lib.srj_plan_temporal_depth(self._h, ctypes.byref(T)))
+        return T.value
+
+    def autotune(self, stream=None):
+        """Pick the fastest temporal depth on this plan's grid; returns (T, us per step)."""
+        T = ctypes.c_int(); us = ctypes.c_float()
+        check(self._lib.srj_plan_autotune(self._h, _stream_ptr(stream), ctypes.byref(T), ctypes.byref(us)))
+        return T.value, us.value
+
     def order(self):
         M = self.info()["M"]
         out = np.empty(M, dtype=np.int32)

@@ -16,7 +16,7 @@ _ROOT = _PKG.parent
 _CSRC = _PKG / "csrc"
 _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
-SOURCES = ["srj_kernels.cu", "srj_plan.cu", "srj_noalloc.cu"]
+SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -95,6 +95,9 @@ SIGNATURES = {
     "srj_plan_destroy": (_I, [_VP]),
     "srj_plan_info": (_I, [_VP, _I64P, _DP, _DP]),
     "srj_plan_order": (_I, [_VP, _I32P]),
+    "srj_plan_set_temporal_depth": (_I, [_VP, _I]),
+    "srj_plan_temporal_depth": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "srj_plan_autotune": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "srj_solve": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
     "srj_steps": (_I, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "srj_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),

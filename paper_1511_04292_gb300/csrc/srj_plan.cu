@@ -171,6 +171,13 @@ struct srj_plan {
     srj::NormScratch ns{};
     double* host_norms = nullptr;  // pinned, 2 doubles
 
+    // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
+    int tdepth = 1;
+    srj::TileMap map_a{}, map_b{}, map_r{};
+    float* e_final = nullptr;  // buffer holding the correction after one cycle
+    int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
+    int* host_err = nullptr;   // pinned copy
+
     cudaStream_t cap = nullptr;             // private stream used for graph capture
     cudaGraphExec_t cycle_exec[2] = {nullptr, nullptr};  // start buffer a / b
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;            // brackets of each cycle graph
@@ -183,11 +190,41 @@ struct srj_plan {
         cudaFree(ua); cudaFree(ub); cudaFree(b);
         cudaFree(ea); cudaFree(eb); cudaFree(r32);
         cudaFree(ns.partials); cudaFree(ns.counter); cudaFree(ns.result);
+        cudaFree(d_err);
         if (host_norms) cudaFreeHost(host_norms);
+        if (host_err) cudaFreeHost(host_err);
     }
 };
 
 namespace {
+
+// Issue `count` FP32 steps of the cycle order from position `first`, starting
+// from buffer ea; returns the buffer that holds the result in *final.
+cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStream_t s, float** final) {
+    const int64_t M = p->M;
+    float* in = p->ea;
+    float* out = p->eb;
+    const srj::TileMap* min = &p->map_a;
+    const srj::TileMap* mout = &p->map_b;
+    cudaError_t err = cudaSuccess;
+    const int T = p->tdepth;
+    for (int64_t k = 0; k < count && err == cudaSuccess;) {
+        const int n = (int)std::min<int64_t>(T, count - k);
+        if (T == 1) {
+            err = srj::launch_sweep_f32(p->g, in, out, p->r32, (float)p->c64[(size_t)((first + k) % M)], s);
+        } else {
+            srj::TbSteps st{};
+            st.T = n;
+            for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
+            err = srj::launch_sweep_f32_tb(p->g, *min, p->map_r, out, st, p->d_err, s);
+        }
+        std::swap(in, out);
+        std::swap(min, mout);
+        k += n;
+    }
+    *final = in;
+    return err;
+}
 
 // Capture one M-cycle of sweeps starting from buffer `start` (0 = a, 1 = b).
 int capture_cycle(srj_plan* p, int start) {
@@ -202,11 +239,7 @@ int capture_cycle(srj_plan* p, int start) {
         }
     } else {
         err = cudaMemsetAsync(p->ea, 0, sizeof(float) * (size_t)p->g.n32, p->cap);
-        for (int64_t k = 0; k < p->M && err == cudaSuccess; ++k) {
-            const bool from_a = (k % 2) == 0;
-            err = srj::launch_sweep_f32(p->g, from_a ? p->ea : p->eb, from_a ? p->eb : p->ea, p->r32,
-                                        (float)p->c64[(size_t)k], p->cap);
-        }
+        if (err == cudaSuccess) err = issue_f32_steps(p, 0, p->M, p->cap, &p->e_final);
     }
     cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
     if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SRJ_CUDA(err); }
@@ -227,10 +260,32 @@ int check_plan(srj_plan_t p) {
 
 int read_norms(srj_plan* p, cudaStream_t s, double* l2, double* linf) {
     SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     *l2 = p->host_norms[0];
     *linf = p->host_norms[1];
+    if (*p->host_err) {
+        cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
+        return fail(SRJ_ERR_TIMEOUT, "a tile load did not complete within its bounded wait");
+    }
     return SRJ_OK;
+}
+
+// Re-capture the cycle graphs (after a change of the temporal depth).
+int recapture(srj_plan* p) {
+    for (auto& ge : p->cycle_exec)
+        if (ge) { cudaGraphExecDestroy(ge); ge = nullptr; }
+    int rc = capture_cycle(p, 0);
+    if (rc == SRJ_OK && p->precision == SRJ_PREC_FP64 && (p->M % 2) == 1) rc = capture_cycle(p, 1);
+    return rc;
+}
+
+int set_depth(srj_plan* p, int T) {
+    if (T < 1 || T > srj::tb_max_steps()) return fail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..%d", srj::tb_max_steps());
+    if (T > 1 && !(p->precision == SRJ_PREC_MIXED && p->g.nd == 2))
+        return fail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for 2-D mixed-precision plans");
+    p->tdepth = T;
+    return recapture(p);
 }
 
 }  // namespace
@@ -351,17 +406,28 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
                      cudaMemset(p->r32, 0, by) == cudaSuccess;
     }
     ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 2 * srj::kMaxNormBlocks) &&
-         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double));
+         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double)) &&
+         alloc((void**)&p->d_err, sizeof(int));
     if (!ok) { cudaGetLastError(); return bail(fail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
     if (cudaMemset(p->ns.counter, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->host_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&p->host_norms, 2 * sizeof(double)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SRJ_ERR_CUDA, "plan setup failed"));
     }
-    int rc = capture_cycle(p, 0);
-    if (rc == SRJ_OK && precision == SRJ_PREC_FP64 && (M % 2) == 1) rc = capture_cycle(p, 1);
+    if (precision == SRJ_PREC_MIXED && ndim == 2) {
+        if (srj::tb_prepare() != cudaSuccess || srj::make_tile_map(p->g, p->ea, &p->map_a) != cudaSuccess ||
+            srj::make_tile_map(p->g, p->eb, &p->map_b) != cudaSuccess ||
+            srj::make_tile_map(p->g, p->r32, &p->map_r) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SRJ_ERR_CUDA, "tensor-map set-up for the blocked sweep failed"));
+        }
+        p->tdepth = 4;
+    }
+    int rc = recapture(p);
     if (rc != SRJ_OK) return bail(rc);
     if (cudaStreamSynchronize(p->cap) != cudaSuccess) return bail(fail(SRJ_ERR_CUDA, "plan setup sync failed"));
     *out = p;
@@ -377,6 +443,58 @@ int srj_plan_destroy(srj_plan_t plan) {
     delete plan;
     if (dev >= 0 && dev != plan->device) cudaSetDevice(dev);
     return SRJ_OK;
+}
+
+int srj_plan_set_temporal_depth(srj_plan_t plan, int T) {
+    int rc = check_plan(plan);
+    if (rc) return rc;
+    return set_depth(plan, T);
+}
+
+int srj_plan_temporal_depth(srj_plan_t plan, int* T) {
+    if (!plan || !T) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    *T = plan->tdepth;
+    return SRJ_OK;
+}
+
+int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_per_step) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int cands[8] = {1, 2, 3, 4, 5, 6, 7, 8};
+    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 8 : 1;
+    const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
+    float best = INFINITY;
+    int bestT = p->tdepth;
+    for (int ci = 0; ci < ncand; ++ci) {
+        p->tdepth = cands[ci];
+        float* fin = nullptr;
+        float ms_best = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            SRJ_CUDA(cudaEventRecord(p->ev0, s));
+            if (p->precision == SRJ_PREC_MIXED) {
+                SRJ_CUDA(issue_f32_steps(p, 0, steps, s, &fin));
+            } else {
+                for (int64_t k = 0; k < steps; ++k) {
+                    const bool a = (k % 2) == 0;
+                    SRJ_CUDA(srj::launch_sweep_f64(p->g, a ? p->ua : p->ub, a ? p->ub : p->ua, p->b,
+                                                   p->c64[(size_t)(k % p->M)], s));
+                }
+            }
+            SRJ_CUDA(cudaEventRecord(p->ev1, s));
+            SRJ_CUDA(cudaEventSynchronize(p->ev1));
+            float ms = 0.f;
+            SRJ_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+            ms_best = std::min(ms_best, ms);
+        }
+        if (ms_best < best) { best = ms_best; bestT = cands[ci]; }
+    }
+    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    if (*p->host_err) { cudaMemset(p->d_err, 0, sizeof(int)); return fail(SRJ_ERR_TIMEOUT, "bounded wait gave up"); }
+    if (best_T) *best_T = bestT;
+    if (best_us_per_step) *best_us_per_step = best * 1000.f / (float)steps;
+    return set_depth(p, bestT);
 }
 
 int srj_plan_info(srj_plan_t plan, int64_t* M, double* kappa_min, double* gmax) {
@@ -432,14 +550,16 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
         SRJ_CUDA(srj::launch_to_f32(p->g, u, p->eb, s));
         SRJ_CUDA(cudaMemsetAsync(p->r32, 0, sizeof(float) * (size_t)p->g.n32, s));
         SRJ_CUDA(srj::launch_source_f32(p->g, p->h2, f, p->r32, s));
-        for (int64_t k = 0; k < count; ++k) {
-            const bool from_a = (k % 2) == 0;
-            SRJ_CUDA(srj::launch_sweep_f32(p->g, from_a ? p->ea : p->eb, from_a ? p->eb : p->ea, p->r32,
-                                           (float)p->c64[(size_t)((first + k) % M)], s));
-        }
-        SRJ_CUDA(srj::launch_from_f32(p->g, (count % 2) ? p->eb : p->ea, u, s));
+        float* fin = nullptr;
+        SRJ_CUDA(issue_f32_steps(p, first, count, s, &fin));
+        SRJ_CUDA(srj::launch_from_f32(p->g, fin, u, s));
     }
+    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
+    if (*p->host_err) {
+        cudaMemset(p->d_err, 0, sizeof(int));
+        return fail(SRJ_ERR_TIMEOUT, "a tile load did not complete within its bounded wait");
+    }
     return SRJ_OK;
 }
 
@@ -493,7 +613,7 @@ int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_
             } else {
                 SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[0], s));
                 SRJ_CUDA(cudaEventRecord(p->ev1, s));
-                SRJ_CUDA(srj::launch_update(p->g, u, (p->M % 2) ? p->eb : p->ea, 1.0 / scale, s));
+                SRJ_CUDA(srj::launch_update(p->g, u, p->e_final, 1.0 / scale, s));
                 SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, p->r32, scale, p->ns, s));
             }
             if ((rc = read_norms(p, s, &l2, &linf))) return rc;

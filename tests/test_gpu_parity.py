@@ -231,3 +231,53 @@ def test_full_size_workload2_mixed_solve():
     nb = sum(np.abs(np.roll(u32, s, axis=a)) for a in (0, 1) for s in (-1, 1))
     bound = 8 * 2.0 ** -24 * (np.abs(u32) + c * (nb + np.abs(h * h * f32) + 4 * np.abs(u32)))
     assert np.all(np.abs(got - ref)[1:-1, 1:-1] <= bound[1:-1, 1:-1])
+
+
+@pytest.mark.parametrize("dims", [(37, 23), (130, 67), (1, 1), (5, 300), (129, 129), (300, 5), (1000, 700)])
+def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
+    """Temporal blocking (T steps per launch from a shared-memory tile) must give
+    exactly the bits of T single-step launches, for every T, for step counts that
+    are not multiples of T, and on grids smaller or ragged against the tile."""
+    omega, q, order = small_schedule(dims, 4)
+    h = 1.0 / (max(dims) + 1)
+    f, u = random_problem(dims, 41)
+    u[tuple(slice(1, -1) for _ in dims)] *= 1e-3  # keep the iterates moderate
+    plan = srj.Plan(dims, h, omega, q, order, "mixed")
+    fd = dev(f)
+    for count, first in [(len(order), 0), (13, 5)]:
+        plan.set_temporal_depth(1)
+        ref = dev(u)
+        plan.steps(fd, ref, first, count)
+        for T in range(2, 9):
+            plan.set_temporal_depth(T)
+            got = dev(u)
+            plan.steps(fd, got, first, count)
+            assert torch.equal(got, ref), (dims, T, count, first)
+
+
+def test_autotune_picks_a_valid_depth_and_solve_still_converges():
+    n = 512
+    dims = (n, n)
+    f, u0 = W.random_smooth_problem_2d(n, 8)
+    plan = srj.Plan.from_table(dims, 8, "mixed")
+    T, us = plan.autotune()
+    assert 1 <= T <= 8 and plan.temporal_depth() == T and us > 0
+    ud = dev(u0)
+    plan.solve(dev(f), ud, 1e-10, 200)
+    r0, _ = oracle.residual(dims, plan.h, f, u0)
+    l2, _ = oracle.residual(dims, plan.h, f, ud.cpu().numpy())
+    assert l2 <= 1e-10 * r0 * (1 + 1e-9)
+
+
+def test_temporal_depth_rules():
+    p64 = srj.Plan((16, 16), 0.1, [1.0], [1], None, "fp64")
+    with pytest.raises(srj.SRJError):
+        p64.set_temporal_depth(4)
+    p3 = srj.Plan((8, 8, 8), 0.1, [1.0], [1], None, "mixed")
+    assert p3.temporal_depth() == 1
+    with pytest.raises(srj.SRJError):
+        p3.set_temporal_depth(2)
+    p2 = srj.Plan((16, 16), 0.1, [1.0], [1], None, "mixed")
+    assert p2.temporal_depth() == 4
+    with pytest.raises(srj.SRJError):
+        p2.set_temporal_depth(9)
