@@ -30,7 +30,7 @@ constexpr int kSY = 64;   // tile rows
 constexpr int kWarps = 8;
 constexpr int kBand = kSY / kWarps;
 constexpr unsigned kTileBytes = kSX * kSY * sizeof(float);
-constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier wait (~seconds), then error
+constexpr unsigned long long kWaitNs = 100000000ull;  // give up on a tile load after 100 ms
 
 __device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -53,6 +53,12 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+__device__ inline unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -93,9 +99,11 @@ k_sweep_f32_tb(const __grid_constant__ CUtensorMap map_e, const __grid_constant_
         tma_load_2d(A, &map_e, &bar, X0 + 3, Y0);  // float32 column of padded x is x + 3
         tma_load_2d(R, &map_r, &bar, X0 + 3, Y0);
     }
-    bool ready = false;
-    for (long long spins = 0; spins < kWaitLimit; ++spins) {
-        if (mbar_try_wait(&bar, 0)) { ready = true; break; }
+    bool ready = mbar_try_wait(&bar, 0);
+    if (!ready) {
+        const unsigned long long t0 = global_ns();
+        while (!(ready = mbar_try_wait(&bar, 0)) && global_ns() - t0 < kWaitNs) {
+        }
     }
     if (__syncthreads_or(!ready)) {  // the whole block gives up together
         if (threadIdx.x == 0) atomicExch(err, 1);
