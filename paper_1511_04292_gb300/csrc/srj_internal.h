@@ -66,11 +66,6 @@ cudaError_t launch_from_f32(const Geom& g, const float* e, double* u, cudaStream
 
 // ---- temporally blocked FP32 sweep (2-D) ----------------------------------
 
-// Opaque storage for a CUtensorMap (128 bytes, 64-byte aligned).
-struct alignas(64) TileMap {
-    unsigned char bytes[128];
-};
-
 // Weights of up to 8 consecutive steps: c[t] = omega / 2d for step t < T.
 struct TbSteps {
     int T;
@@ -79,13 +74,10 @@ struct TbSteps {
 
 int tb_max_steps();
 cudaError_t tb_prepare();  // kernel attributes (dynamic shared memory)
-// 2-D tensor map over a pitched float32 buffer: rows of p32 floats, box 128 x 64.
-cudaError_t make_tile_map(const Geom& g, const float* base, TileMap* out);
-// T = steps.T consecutive FP32 steps in one launch: reads the buffer behind
-// map_in and the defect behind map_r, writes the interior of eout.  Sets *err
-// to 1 if a bounded wait for the tile loads gives up.
-cudaError_t launch_sweep_f32_tb(const Geom& g, const TileMap& map_in, const TileMap& map_r, float* eout,
-                                const TbSteps& steps, int* err, cudaStream_t s);
+// T = steps.T consecutive FP32 steps in one launch: reads ein and the defect
+// rin (pitched float32), writes the interior of eout (eout != ein).
+cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
+                                const TbSteps& steps, cudaStream_t s);
 
 // grad_g[ghost q] = sum of lambda over the interior neighbours of q; interior 0.
 cudaError_t launch_boundary_adjoint(const Geom& g, const double* lambda, double* grad_g, cudaStream_t s);

@@ -173,7 +173,6 @@ struct srj_plan {
 
     // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
     int tdepth = 1;
-    srj::TileMap map_a{}, map_b{}, map_r{};
     float* e_final = nullptr;  // buffer holding the correction after one cycle
     int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
     int* host_err = nullptr;   // pinned copy
@@ -204,8 +203,6 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
     const int64_t M = p->M;
     float* in = p->ea;
     float* out = p->eb;
-    const srj::TileMap* min = &p->map_a;
-    const srj::TileMap* mout = &p->map_b;
     cudaError_t err = cudaSuccess;
     const int T = p->tdepth;
     for (int64_t k = 0; k < count && err == cudaSuccess;) {
@@ -216,10 +213,9 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
             srj::TbSteps st{};
             st.T = n;
             for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
-            err = srj::launch_sweep_f32_tb(p->g, *min, p->map_r, out, st, p->d_err, s);
+            err = srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, s);
         }
         std::swap(in, out);
-        std::swap(min, mout);
         k += n;
     }
     *final = in;
@@ -419,11 +415,9 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
         return bail(fail(SRJ_ERR_CUDA, "plan setup failed"));
     }
     if (precision == SRJ_PREC_MIXED && ndim == 2) {
-        if (srj::tb_prepare() != cudaSuccess || srj::make_tile_map(p->g, p->ea, &p->map_a) != cudaSuccess ||
-            srj::make_tile_map(p->g, p->eb, &p->map_b) != cudaSuccess ||
-            srj::make_tile_map(p->g, p->r32, &p->map_r) != cudaSuccess) {
+        if (srj::tb_prepare() != cudaSuccess) {
             cudaGetLastError();
-            return bail(fail(SRJ_ERR_CUDA, "tensor-map set-up for the blocked sweep failed"));
+            return bail(fail(SRJ_ERR_CUDA, "set-up of the blocked sweep failed"));
         }
         p->tdepth = 4;
     }

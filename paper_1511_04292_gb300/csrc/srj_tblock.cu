@@ -3,8 +3,7 @@
 // T consecutive weighted-Jacobi steps (Sect. 3.1, Eq. 2nd-order_CD with the
 // Poisson source of Sect. 5.1), each with its own weight of the cycle order
 // (Sect. 2), are applied to one tile per HBM round trip: the tile of e and of
-// the FP32 defect r is brought into shared memory by two TMA tensor loads
-// (cp.async.bulk.tensor, completion on an mbarrier), the T steps run out of
+// the FP32 defect r is loaded into shared memory once, the T steps run out of
 // shared memory and registers, and only the tile's centre is written back.
 //
 // Tile: 128 columns x 64 rows in shared memory.  One warp spans the 128
@@ -17,8 +16,6 @@
 // expression, so T blocked steps reproduce T unblocked steps bit for bit.
 #include "srj_internal.h"
 
-#include <cuda.h>
-
 #include <algorithm>
 
 namespace srj {
@@ -30,43 +27,6 @@ constexpr int kSY = 64;   // tile rows
 constexpr int kWarps = 8;
 constexpr int kBand = kSY / kWarps;
 constexpr unsigned kTileBytes = kSX * kSY * sizeof(float);
-constexpr unsigned long long kWaitNs = 100000000ull;  // give up on a tile load after 100 ms
-
-__device__ inline uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ inline unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
-        : "memory");
-}
 
 __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) {
     return fmaf(c, fmaf(-two_d, cc, nb + rr), cc);
@@ -74,13 +34,12 @@ __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) 
 
 template <int T>
 __global__ void __launch_bounds__(kWarps * 32, 3)
-k_sweep_f32_tb(const __grid_constant__ CUtensorMap map_e, const __grid_constant__ CUtensorMap map_r,
-               float* __restrict__ eout, Geom g, TbSteps steps, int* __restrict__ err) {
+k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
+               TbSteps steps) {
     constexpr int HX = T <= 4 ? 4 : 8;
     extern __shared__ unsigned char smem_raw[];
     float* A = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float* R = A + kSX * kSY;
-    __shared__ __align__(8) uint64_t bar;
 
     constexpr int TX = kSX - 2 * HX;
     constexpr int TY = kSY - 2 * T;
@@ -89,26 +48,34 @@ k_sweep_f32_tb(const __grid_constant__ CUtensorMap map_e, const __grid_constant_
     const int X0 = 1 + TX * (int)blockIdx.x - HX;  // padded x of tile column 0
     const int Y0 = 1 + TY * (int)blockIdx.y - T;   // padded y of tile row 0
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, 2 * kTileBytes);
-        tma_load_2d(A, &map_e, &bar, X0 + 3, Y0);  // float32 column of padded x is x + 3
-        tma_load_2d(R, &map_r, &bar, X0 + 3, Y0);
-    }
-    bool ready = mbar_try_wait(&bar, 0);
-    if (!ready) {
-        const unsigned long long t0 = global_ns();
-        while (!(ready = mbar_try_wait(&bar, 0)) && global_ns() - t0 < kWaitNs) {
+    // Tile fill: float4 loads of e and r; float32 column of padded x is x + 3,
+    // a multiple of 4 here, so each float4 lies wholly inside or outside the
+    // buffer (rows 0..rows-1, columns 0..p32-1); outside ones read as zero.
+    {
+        const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
+        const int col = X0 + 3 + 4 * lane;
+        const bool colok = col >= 0 && col + 4 <= g.p32;
+        float4 ve[kBand], vr[kBand];
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            const int64_t y = (int64_t)Y0 + row;
+            ve[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            vr[i] = ve[i];
+            if (colok && y >= 0 && y < rows) {
+                const int64_t off = y * g.p32 + col;
+                ve[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+                vr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            reinterpret_cast<float4*>(A)[row * 32 + lane] = ve[i];
+            reinterpret_cast<float4*>(R)[row * 32 + lane] = vr[i];
         }
     }
-    if (__syncthreads_or(!ready)) {  // the whole block gives up together
-        if (threadIdx.x == 0) atomicExch(err, 1);
-        return;
-    }
+    __syncthreads();
 
     const float two_d = 4.0f;
     bool inx[4];
@@ -181,44 +148,11 @@ k_sweep_f32_tb(const __grid_constant__ CUtensorMap map_e, const __grid_constant_
     }
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encoder() {
-    static EncodeTiled fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    }
-    return fn;
-}
-
 size_t smem_bytes() { return 2 * (size_t)kTileBytes + 128; }
 
 }  // namespace
 
 int tb_max_steps() { return 8; }
-
-cudaError_t make_tile_map(const Geom& g, const float* base, TileMap* out) {
-    static_assert(sizeof(TileMap) >= sizeof(CUtensorMap), "TileMap too small");
-    EncodeTiled enc = encoder();
-    if (!enc) return cudaErrorNotSupported;
-    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
-    cuuint64_t dims[2] = {(cuuint64_t)g.p32, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)g.p32 * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)kSX, (cuuint32_t)kSY};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(reinterpret_cast<CUtensorMap*>(out->bytes), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                     const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
 
 template <int T>
 cudaError_t set_attr() {
@@ -226,9 +160,9 @@ cudaError_t set_attr() {
 }
 
 template <int T>
-void launch_T(dim3 grd, cudaStream_t s, const CUtensorMap& me, const CUtensorMap& mr, float* eout, const Geom& g,
-              const TbSteps& st, int* err) {
-    k_sweep_f32_tb<T><<<grd, kWarps * 32, smem_bytes(), s>>>(me, mr, eout, g, st, err);
+void launch_T(dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
+              const TbSteps& st) {
+    k_sweep_f32_tb<T><<<grd, kWarps * 32, smem_bytes(), s>>>(ein, rin, eout, g, st);
 }
 
 cudaError_t tb_prepare() {
@@ -242,23 +176,23 @@ cudaError_t tb_prepare() {
     return e;
 }
 
-cudaError_t launch_sweep_f32_tb(const Geom& g, const TileMap& map_in, const TileMap& map_r, float* eout,
-                                const TbSteps& steps, int* err, cudaStream_t s) {
+cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
+                                const TbSteps& steps, cudaStream_t s) {
     if (g.nd != 2 || steps.T < 1 || steps.T > 8) return cudaErrorInvalidValue;
-    const CUtensorMap& me = *reinterpret_cast<const CUtensorMap*>(map_in.bytes);
-    const CUtensorMap& mr = *reinterpret_cast<const CUtensorMap*>(map_r.bytes);
+    const float* me = ein;
+    const float* mr = rin;
     const int HX = steps.T <= 4 ? 4 : 8;
     const int TX = kSX - 2 * HX, TY = kSY - 2 * steps.T;
     dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
     switch (steps.T) {
-        case 1: launch_T<1>(grd, s, me, mr, eout, g, steps, err); break;
-        case 2: launch_T<2>(grd, s, me, mr, eout, g, steps, err); break;
-        case 3: launch_T<3>(grd, s, me, mr, eout, g, steps, err); break;
-        case 4: launch_T<4>(grd, s, me, mr, eout, g, steps, err); break;
-        case 5: launch_T<5>(grd, s, me, mr, eout, g, steps, err); break;
-        case 6: launch_T<6>(grd, s, me, mr, eout, g, steps, err); break;
-        case 7: launch_T<7>(grd, s, me, mr, eout, g, steps, err); break;
-        default: launch_T<8>(grd, s, me, mr, eout, g, steps, err); break;
+        case 1: launch_T<1>(grd, s, me, mr, eout, g, steps); break;
+        case 2: launch_T<2>(grd, s, me, mr, eout, g, steps); break;
+        case 3: launch_T<3>(grd, s, me, mr, eout, g, steps); break;
+        case 4: launch_T<4>(grd, s, me, mr, eout, g, steps); break;
+        case 5: launch_T<5>(grd, s, me, mr, eout, g, steps); break;
+        case 6: launch_T<6>(grd, s, me, mr, eout, g, steps); break;
+        case 7: launch_T<7>(grd, s, me, mr, eout, g, steps); break;
+        default: launch_T<8>(grd, s, me, mr, eout, g, steps); break;
     }
     return cudaGetLastError();
 }
