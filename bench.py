@@ -55,6 +55,7 @@ def parse():
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
+    ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
     return ap.parse_args()
 
 
@@ -65,6 +66,8 @@ def run_kernel_case(args):
     n = args.n
     torch.cuda.set_device(0)
     plan = srj.Plan((n, n), 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
+    if args.T is not None:
+        plan.set_temporal_depth(args.T)
     f = torch.from_numpy(W.random_field((n, n), 1)).cuda()
     u = torch.from_numpy(W.random_field((n, n), 2)).cuda()
     plan.steps(f, u, 0, args.count)
