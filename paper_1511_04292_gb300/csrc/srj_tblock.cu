@@ -3,12 +3,13 @@
 // T consecutive weighted-Jacobi steps (Sect. 3.1, Eq. 2nd-order_CD with the
 // Poisson source of Sect. 5.1), each with its own weight of the cycle order
 // (Sect. 2), are applied to one tile per HBM round trip: the tile of e and of
-// the FP32 defect r is loaded into shared memory once, the T steps run out of
-// shared memory and registers, and only the tile's centre is written back.
+// the FP32 defect r is loaded once, the T steps run out of registers (band
+// edges exchanged through shared memory), and only the tile's centre is
+// written back.
 //
-// Tile: 128 columns x 64 rows in shared memory.  One warp spans the 128
-// columns (a float4 per lane), so the left / right neighbours come from warp
-// shuffles; each of the 8 warps owns a band of 8 rows.  After step t the
+// Tile: 128 columns x 64 rows.  One warp spans the 128 columns (a float4 per
+// lane), so the left / right neighbours come from warp shuffles; each of the
+// 8 warps owns a band of 8 rows, held in registers for all T steps.  After step t the
 // values within t cells of the tile edge are stale; with a halo of HX >= T
 // columns and T rows the centre (128 - 2 HX) x (64 - 2 T) is exact.  Points
 // of the Dirichlet ghost layer and points outside the grid keep their loaded
@@ -32,123 +33,119 @@ __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) 
     return fmaf(c, fmaf(-two_d, cc, nb + rr), cc);
 }
 
+// One warp's band of kBand rows lives in registers for all T steps: e[i]
+// (float4, 4 consecutive columns per lane) and the defect rr[i].  Only the
+// band's top and bottom rows cross warps, through a double-buffered shared
+// slot, so each step costs one barrier and four shared-memory accesses per lane.
+template <int T, bool MASKED>
+__device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr)[kBand], float4* xch,
+                                           const TbSteps& steps, int lane, int w, const bool (&inx)[4],
+                                           const bool (&iny)[kBand]) {
+    const float two_d = 4.0f;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const float c = steps.c[t];
+        float4* slot = xch + (t & 1) * (2 * kWarps * 32);
+        slot[(2 * w) * 32 + lane] = e[0];              // top row of this band
+        slot[(2 * w + 1) * 32 + lane] = e[kBand - 1];  // bottom row
+        __syncthreads();
+        const float4 above = (w > 0) ? slot[(2 * (w - 1) + 1) * 32 + lane] : zero;
+        const float4 below = (w + 1 < kWarps) ? slot[(2 * (w + 1)) * 32 + lane] : zero;
+        float4 up = above;  // old value of the row above the one being updated
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const float4 cur = e[i];
+            const float4 dn = (i + 1 < kBand) ? e[i + 1] : below;
+            float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            if (lane == 0) lf = 0.f;
+            if (lane == 31) rt = 0.f;
+            float4 o;
+            o.x = upd(c, two_d, cur.x, ((lf + cur.y) + up.x) + dn.x, rr[i].x);
+            o.y = upd(c, two_d, cur.y, ((cur.x + cur.z) + up.y) + dn.y, rr[i].y);
+            o.z = upd(c, two_d, cur.z, ((cur.y + cur.w) + up.z) + dn.z, rr[i].z);
+            o.w = upd(c, two_d, cur.w, ((cur.z + rt) + up.w) + dn.w, rr[i].w);
+            if (MASKED) {
+                o.x = (iny[i] && inx[0]) ? o.x : cur.x;
+                o.y = (iny[i] && inx[1]) ? o.y : cur.y;
+                o.z = (iny[i] && inx[2]) ? o.z : cur.z;
+                o.w = (iny[i] && inx[3]) ? o.w : cur.w;
+            }
+            up = cur;
+            e[i] = o;
+        }
+    }
+}
+
 template <int T>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+__global__ void __launch_bounds__(kWarps * 32, 2)
 k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
                TbSteps steps) {
     constexpr int HX = T <= 4 ? 4 : 8;
-    extern __shared__ unsigned char smem_raw[];
-    float* A = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float* R = A + kSX * kSY;
-
     constexpr int TX = kSX - 2 * HX;
     constexpr int TY = kSY - 2 * T;
+    __shared__ float4 xch[2 * 2 * kWarps * 32];  // [slot][warp][top/bottom][lane]
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int X0 = 1 + TX * (int)blockIdx.x - HX;  // padded x of tile column 0
     const int Y0 = 1 + TY * (int)blockIdx.y - T;   // padded y of tile row 0
 
-    // Tile fill: float4 loads of e and r; float32 column of padded x is x + 3,
-    // a multiple of 4 here, so each float4 lies wholly inside or outside the
-    // buffer (rows 0..rows-1, columns 0..p32-1); outside ones read as zero.
-    {
-        const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
-        const int col = X0 + 3 + 4 * lane;
-        const bool colok = col >= 0 && col + 4 <= g.p32;
-        float4 ve[kBand], vr[kBand];
+    // Band fill: float4 loads of e and r straight into registers.  The float32
+    // column of padded x is x + 3, a multiple of 4 here, so each float4 lies
+    // wholly inside or outside the buffer (rows 0..rows-1, columns 0..p32-1);
+    // outside ones read as zero.
+    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
+    const int col = X0 + 3 + 4 * lane;
+    const bool colok = col >= 0 && col + 4 <= g.p32;
+    float4 e[kBand], rr[kBand];
+    bool iny[kBand];
 #pragma unroll
-        for (int i = 0; i < kBand; ++i) {
-            const int row = w * kBand + i;
-            const int64_t y = (int64_t)Y0 + row;
-            ve[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            vr[i] = ve[i];
-            if (colok && y >= 0 && y < rows) {
-                const int64_t off = y * g.p32 + col;
-                ve[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
-                vr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
-            }
+    for (int i = 0; i < kBand; ++i) {
+        const int64_t y = (int64_t)Y0 + w * kBand + i;
+        e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rr[i] = e[i];
+        if (colok && y >= 0 && y < rows) {
+            const int64_t off = y * g.p32 + col;
+            e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+            rr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
         }
-#pragma unroll
-        for (int i = 0; i < kBand; ++i) {
-            const int row = w * kBand + i;
-            reinterpret_cast<float4*>(A)[row * 32 + lane] = ve[i];
-            reinterpret_cast<float4*>(R)[row * 32 + lane] = vr[i];
-        }
+        iny[i] = y >= 1 && y <= g.ny;
     }
-    __syncthreads();
-
-    const float two_d = 4.0f;
     bool inx[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int x = X0 + 4 * lane + j;
         inx[j] = x >= 1 && x <= g.nx;
     }
-    const float4* A4 = reinterpret_cast<const float4*>(A);
-    const float4* R4 = reinterpret_cast<const float4*>(R);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int r0 = w * kBand;
+    // tiles whose every point is an interior grid point need no masking
+    const bool interior = X0 >= 1 && X0 + kSX - 1 <= g.nx && Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
+    if (interior) band_steps<T, false>(e, rr, xch, steps, lane, w, inx, iny);
+    else          band_steps<T, true>(e, rr, xch, steps, lane, w, inx, iny);
 
+    // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
+    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+    if (lane < lane_lo || lane >= lane_hi) return;
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const float c = steps.c[t];
-        float4 out[kBand];
-        float4 up = (r0 > 0) ? A4[(r0 - 1) * 32 + lane] : zero;
-        float4 cur = A4[r0 * 32 + lane];
-#pragma unroll
-        for (int i = 0; i < kBand; ++i) {
-            const int row = r0 + i;
-            const float4 dn = (row + 1 < kSY) ? A4[(row + 1) * 32 + lane] : zero;
-            const float4 rr = R4[row * 32 + lane];
-            float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
-            float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            if (lane == 0) lf = 0.f;
-            if (lane == 31) rt = 0.f;
-            const int y = Y0 + row;
-            const bool iny = y >= 1 && y <= g.ny;
-            float4 o;
-            o.x = upd(c, two_d, cur.x, ((lf + cur.y) + up.x) + dn.x, rr.x);
-            o.y = upd(c, two_d, cur.y, ((cur.x + cur.z) + up.y) + dn.y, rr.y);
-            o.z = upd(c, two_d, cur.z, ((cur.y + cur.w) + up.z) + dn.z, rr.z);
-            o.w = upd(c, two_d, cur.w, ((cur.z + rt) + up.w) + dn.w, rr.w);
-            o.x = (iny && inx[0]) ? o.x : cur.x;
-            o.y = (iny && inx[1]) ? o.y : cur.y;
-            o.z = (iny && inx[2]) ? o.z : cur.z;
-            o.w = (iny && inx[3]) ? o.w : cur.w;
-            out[i] = o;
-            up = cur;
-            cur = dn;
-        }
-        if (t + 1 < T) {
-            __syncthreads();  // every warp has read the old values
-#pragma unroll
-            for (int i = 0; i < kBand; ++i) reinterpret_cast<float4*>(A)[(r0 + i) * 32 + lane] = out[i];
-            __syncthreads();
+    for (int i = 0; i < kBand; ++i) {
+        const int row = w * kBand + i;
+        if (row < T || row >= T + TY) continue;
+        const int y = Y0 + row;
+        if (y < 1 || y > g.ny) continue;
+        const int x = X0 + 4 * lane;
+        float* dst = eout + (int64_t)y * g.p32 + x + 3;  // 16-byte aligned
+        if (inx[0] && inx[3]) {
+            *reinterpret_cast<float4*>(dst) = e[i];
         } else {
-            const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;  // centre columns
-            if (lane < lane_lo || lane >= lane_hi) return;
-#pragma unroll
-            for (int i = 0; i < kBand; ++i) {
-                const int row = r0 + i;
-                if (row < T || row >= T + TY) continue;
-                const int y = Y0 + row;
-                if (y < 1 || y > g.ny) continue;
-                const int x = X0 + 4 * lane;
-                float* dst = eout + (int64_t)y * g.p32 + x + 3;  // 16-byte aligned
-                if (inx[0] && inx[3]) {
-                    *reinterpret_cast<float4*>(dst) = out[i];
-                } else {
-                    if (inx[0]) dst[0] = out[i].x;
-                    if (inx[1]) dst[1] = out[i].y;
-                    if (inx[2]) dst[2] = out[i].z;
-                    if (inx[3]) dst[3] = out[i].w;
-                }
-            }
+            if (inx[0]) dst[0] = e[i].x;
+            if (inx[1]) dst[1] = e[i].y;
+            if (inx[2]) dst[2] = e[i].z;
+            if (inx[3]) dst[3] = e[i].w;
         }
     }
 }
 
-size_t smem_bytes() { return 2 * (size_t)kTileBytes + 128; }
+size_t smem_bytes() { return 0; }
 
 }  // namespace
 
