@@ -199,6 +199,52 @@ int srj_schedule_check(int P, const double *omega, const int32_t *q, double kapp
  */
 int srj_schedule_order(int P, const double *omega, const int32_t *q, double kappa_min, int32_t *order_out);
 
+/*
+ * Batched solver: many independent 2-D problems, each with its own size and
+ * SRJ schedule, solved together in mixed precision (FP32 M-cycles on the defect
+ * equation inside FP64 correction, as SRJ_PREC_MIXED).  One phase advances every
+ * unfinished problem by up to T steps of its own cycle order in one blocked
+ * sweep launch over the tiles of all problems, then updates, checks the
+ * residual of and restarts the problems whose cycle ended.  A CUDA graph of
+ * several phases is replayed until every problem has converged, failed, or run
+ * max_cycles cycles.  The paper's method per problem is Sect. 2 / 3.1 / 5.1; the
+ * batching is this library's.
+ */
+typedef struct srj_batch *srj_batch_t;
+
+typedef struct srj_batch_problem {
+    int64_t nx, ny;        /* interior points (1..65536 each)                      */
+    double h;              /* mesh spacing                                          */
+    int32_t P;             /* levels                                                */
+    const double *omega;   /* host, P weights                                       */
+    const int32_t *q;      /* host, P repetitions                                   */
+    const int32_t *order;  /* host, M level indices, or NULL for the drift order   */
+} srj_batch_problem_t;
+
+/* Build a batch (copies every schedule; allocates 3 pitched float32 grids per
+ * problem).  temporal_depth: steps per sweep launch, 1..8, 0 = 8.  Each
+ * problem's integer scheme must contract on its grid (SRJ_ERR_BAD_SCHEDULE). */
+int srj_batch_create(srj_batch_t *batch, int nprob, const srj_batch_problem_t *problems, int temporal_depth);
+
+int srj_batch_destroy(srj_batch_t batch);
+
+/* Sizes of a batch (host outputs, each may be NULL). */
+int srj_batch_info(srj_batch_t batch, int64_t *total_points, int64_t *tiles, int *temporal_depth, int64_t *sum_M);
+
+/*
+ * srj_batch_solve -- f, u: HOST arrays of nprob DEVICE pointers, each a padded
+ * float64 grid of its problem (layout of srj_solve; u: initial guess with the
+ * Dirichlet data in its ghost layer, overwritten by the iterate).  stats: host
+ * array of nprob entries or NULL (sweep_ms = device time of the whole batch).
+ * device_ms: host, may be NULL.  Returns SRJ_OK when every problem reached
+ * ||r||_2 / ||r_0||_2 <= tol, else the first failing status.  Blocks the host.
+ */
+int srj_batch_solve(srj_batch_t batch, const double *const *f, double *const *u, double tol, int64_t max_cycles,
+                    void *stream, srj_stats_t *stats, double *device_ms);
+
+/* Text of the last batch error on the calling thread. */
+const char *srj_batch_last_error(void);
+
 /* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 

@@ -19,7 +19,7 @@ import numpy as np
 from . import schedules
 from ._native import SRJError, Stats, build, check, lib
 
-__all__ = ["Plan", "SRJError", "build", "lib", "schedules", "kappa_min", "PREC_FP64", "PREC_MIXED"]
+__all__ = ["Plan", "Batch", "SRJError", "build", "lib", "schedules", "kappa_min", "PREC_FP64", "PREC_MIXED"]
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -149,3 +149,64 @@ class Plan:
         check(self._lib.srj_boundary_adjoint(self._h, _dev_ptr(lam, self.shape, "lam"),
                                              _dev_ptr(grad_g, self.shape, "grad_g", True), _stream_ptr(stream)))
         return grad_g
+
+
+class Batch:
+    """Many independent 2-D problems solved together (mixed precision).
+
+    problems: list of dicts with keys dims=(nx, ny), h, omega, q, order (or None).
+    """
+
+    def __init__(self, problems, temporal_depth=0):
+        from ._native import BatchProblem
+        self._lib = lib()
+        self._keep = []
+        arr = (BatchProblem * len(problems))()
+        self.shapes = []
+        for i, pr in enumerate(problems):
+            nx, ny = (int(v) for v in pr["dims"])
+            om = np.ascontiguousarray(pr["omega"], dtype=np.float64)
+            qq = np.ascontiguousarray(pr["q"], dtype=np.int32)
+            od = None if pr.get("order") is None else np.ascontiguousarray(pr["order"], dtype=np.int32)
+            self._keep += [om, qq, od]
+            arr[i].nx, arr[i].ny, arr[i].h, arr[i].P = nx, ny, float(pr["h"]), len(om)
+            arr[i].omega = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].q = qq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            arr[i].order = None if od is None else od.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            self.shapes.append((ny + 2, nx + 2))
+        h = ctypes.c_void_p()
+        check(self._lib.srj_batch_create(ctypes.byref(h), len(problems), arr, int(temporal_depth)),
+              "srj_batch_last_error")
+        self._h = h
+        self.n = len(problems)
+
+    def info(self):
+        pts = ctypes.c_int64(); tiles = ctypes.c_int64(); T = ctypes.c_int(); sm = ctypes.c_int64()
+        check(self._lib.srj_batch_info(self._h, ctypes.byref(pts), ctypes.byref(tiles), ctypes.byref(T),
+                                       ctypes.byref(sm)), "srj_batch_last_error")
+        return dict(points=pts.value, tiles=tiles.value, temporal_depth=T.value, sum_M=sm.value)
+
+    def solve(self, fs, us, tol, max_cycles, stream=None, raise_on_fail=True):
+        """fs, us: lists of float64 CUDA tensors (padded layout per problem); us updated in place."""
+        if len(fs) != self.n or len(us) != self.n:
+            raise ValueError("need one f and one u per problem")
+        fp = (ctypes.c_void_p * self.n)(*[_dev_ptr(f, s, "f").value for f, s in zip(fs, self.shapes)])
+        up = (ctypes.c_void_p * self.n)(*[_dev_ptr(u, s, "u").value for u, s in zip(us, self.shapes)])
+        st = (Stats * self.n)()
+        ms = ctypes.c_double()
+        rc = self._lib.srj_batch_solve(self._h, fp, up, float(tol), int(max_cycles), _stream_ptr(stream), st,
+                                       ctypes.byref(ms))
+        if raise_on_fail:
+            check(rc, "srj_batch_last_error")
+        return [s.as_dict() for s in st], ms.value, rc
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.srj_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

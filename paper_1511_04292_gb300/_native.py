@@ -16,7 +16,7 @@ _ROOT = _PKG.parent
 _CSRC = _PKG / "csrc"
 _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
-SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_noalloc.cu"]
+SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_batch.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -85,6 +85,12 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("h", ctypes.c_double), ("P", ctypes.c_int32),
+                ("omega", ctypes.POINTER(ctypes.c_double)), ("q", ctypes.POINTER(ctypes.c_int32)),
+                ("order", ctypes.POINTER(ctypes.c_int32))]
+
+
 # name -> (restype, argtypes)
 _VP, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -107,6 +113,12 @@ SIGNATURES = {
     "srj_schedule_order": (_I, [_I, _DP, _I32P, _D, _I32P]),
     "srj_steps_f32_noalloc": (_I, [_I, _I64P, _D, _I64, _DP, _VP, _VP, _VP]),
     "srj_noalloc_last_error": (ctypes.c_char_p, []),
+    "srj_batch_create": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(BatchProblem), _I]),
+    "srj_batch_destroy": (_I, [_VP]),
+    "srj_batch_info": (_I, [_VP, _I64P, _I64P, ctypes.POINTER(ctypes.c_int), _I64P]),
+    "srj_batch_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I64, _VP,
+                             ctypes.POINTER(Stats), _DP]),
+    "srj_batch_last_error": (ctypes.c_char_p, []),
     "srj_last_error": (ctypes.c_char_p, []),
     "srj_version": (ctypes.c_char_p, []),
 }
@@ -128,8 +140,8 @@ def lib():
     return _lib
 
 
-def check(status):
+def check(status, errfn="srj_last_error"):
     if status != 0:
-        msg = lib().srj_last_error().decode(errors="replace")
+        msg = getattr(lib(), errfn)().decode(errors="replace")
         raise SRJError(status, "%s: %s" % (STATUS.get(status, "?"), msg))
     return status

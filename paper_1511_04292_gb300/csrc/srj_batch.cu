@@ -1,0 +1,464 @@
+// Batched SRJ: many independent 2-D Dirichlet Poisson problems of different
+// sizes, each with its own schedule (Sect. 2: weights omega_i repeated q_i
+// times per M-cycle), solved together in mixed precision (FP32 cycles on the
+// defect equation inside FP64 correction, as in srj_solve).
+//
+// Work is organised in phases.  One phase is five launches:
+//   1. blocked FP32 sweep over the tiles of every active problem; each problem
+//      advances by n = min(T, M - k) steps of its own cycle order;
+//   2. advance: per problem, k += n, swap the correction buffers, flag the end
+//      of a cycle;
+//   3. FP64 update u += e / s for the problems whose cycle ended;
+//   4. FP64 residual r = b - A u for them (written as FP32 r * s, with L2 / max
+//      partial sums per row block);
+//   5. finalize: per problem, norms, convergence test at the cycle end
+//      (Sect. 4.1 monitor on b - A u), restart of the next cycle from e = 0.
+// Kernel boundaries order the phases (no device-side waits); every launch reads
+// the per-problem state from device memory, so one CUDA graph of G phases is
+// captured at creation and replayed until no problem is active.
+#include "srj_internal.h"
+#include "../../include/srj.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_batch_err;
+
+int bfail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_batch_err = buf;
+    return code;
+}
+
+#define SRJ_BCUDA(call)                                                                              \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(SRJ_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                                  \
+    } while (0)
+
+constexpr int kRowsPerBlock = 16;
+constexpr int kThreads = 256;
+constexpr int kPhasesPerGraph = 16;
+
+enum { kFinInit0 = 0, kFinInit1 = 1, kFinCycle = 2 };
+
+__global__ void k_batch_advance(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st, int nprob,
+                                int T) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    srj::BatchState s = st[p];
+    if (!s.active) return;
+    const int n = min(T, probs[p].M - s.k);
+    s.k += n;
+    s.cur ^= 1;
+    s.fresh = 0;
+    if (s.k == probs[p].M) s.cycle_end = 1;
+    st[p] = s;
+}
+
+// u += inv_scale * e on the rows of one row block, for problems at a cycle end.
+__global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
+                               const int2* __restrict__ rowblocks) {
+    const int2 rb = rowblocks[blockIdx.x];
+    const srj::BatchState s = st[rb.x];
+    if (!s.active || !s.cycle_end) return;
+    const srj::BatchProb P = probs[rb.x];
+    const float* e = s.cur ? P.eb : P.ea;
+    const int y1 = min(rb.y + kRowsPerBlock - 1, P.ny);
+    const int64_t sx = P.nx + 2;
+    for (int y = rb.y; y <= y1; ++y)
+        for (int x = threadIdx.x + 1; x <= P.nx; x += blockDim.x)
+            P.u[(int64_t)y * sx + x] += s.inv_scale * (double)e[(int64_t)y * P.p32 + x + 3];
+}
+
+// r = (h^2 f + sum nbrs u) - 4 u in the oracle's operation order; optional FP32
+// defect r * scale; per-block L2 / max partials.  `all`: every active problem
+// (initial residual), otherwise only problems at a cycle end.
+__global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
+                                 const int2* __restrict__ rowblocks, double* __restrict__ partials, int write_r32,
+                                 int all) {
+    __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
+    const int2 rb = rowblocks[blockIdx.x];
+    const srj::BatchState s = st[rb.x];
+    const bool work = s.active && (all || s.cycle_end);
+    double ss = 0.0, mx = 0.0;
+    if (work) {
+        const srj::BatchProb P = probs[rb.x];
+        const int y1 = min(rb.y + kRowsPerBlock - 1, P.ny);
+        const int64_t sx = P.nx + 2;
+        for (int y = rb.y; y <= y1; ++y) {
+            for (int x = threadIdx.x + 1; x <= P.nx; x += blockDim.x) {
+                const int64_t q = (int64_t)y * sx + x;
+                const double uc = P.u[q];
+                double sm = __dadd_rn(P.u[q - 1], P.u[q + 1]);
+                sm = __dadd_rn(sm, P.u[q - sx]);
+                sm = __dadd_rn(sm, P.u[q + sx]);
+                const double t = __dadd_rn(sm, __dmul_rn(P.h2, P.f[q]));
+                const double r = __dsub_rn(t, __dmul_rn(4.0, uc));
+                if (write_r32) P.r32[(int64_t)y * P.p32 + x + 3] = (float)(r * s.scale);
+                ss = fma(r, r, ss);
+                mx = fmax(mx, fabs(r));
+            }
+        }
+    }
+    if (!work) return;  // uniform over the block
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_down_sync(0xffffffffu, ss, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sh_ss[w] = ss; sh_mx[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += sh_ss[i]; m = fmax(m, sh_mx[i]); }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = (a == a) ? m : a;
+    }
+}
+
+__global__ void k_batch_finalize(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st,
+                                 const double* __restrict__ partials, int nprob, int mode, double tol,
+                                 int max_cycles) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    srj::BatchState s = st[p];
+    if (!s.active) return;
+    if (mode == kFinInit1) { s.cycle_end = 0; s.fresh = 1; s.k = 0; st[p] = s; return; }
+    if (mode == kFinCycle && !s.cycle_end) return;
+    double a = 0.0, m = 0.0;
+    for (int b = probs[p].rb_begin; b < probs[p].rb_end; ++b) {
+        a += partials[2 * b];
+        m = fmax(m, partials[2 * b + 1]);
+    }
+    const double l2 = sqrt(a);
+    s.l2 = l2;
+    s.linf = (a == a) ? m : a;
+    if (mode == kFinInit0) {
+        s.r0 = l2;
+        if (!isfinite(l2)) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
+        else if (l2 == 0.0 || !(tol < 1.0)) { s.status = SRJ_OK; s.active = 0; }
+        else {
+            int ex = 0;
+            frexp(s.linf, &ex);
+            s.scale = ldexp(1.0, -ex);
+            s.inv_scale = ldexp(1.0, ex);
+        }
+        st[p] = s;
+        return;
+    }
+    s.cycles += 1;
+    s.cycle_end = 0;
+    if (!isfinite(l2) || l2 > 1e6 * s.r0) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
+    else if (l2 / s.r0 <= tol) { s.status = SRJ_OK; s.active = 0; }
+    else if (s.cycles >= max_cycles) { s.status = SRJ_ERR_NOT_CONVERGED; s.active = 0; }
+    else { s.k = 0; s.fresh = 1; }
+    st[p] = s;
+}
+
+__global__ void k_batch_count(const srj::BatchState* __restrict__ st, int nprob, int* __restrict__ out) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) c += st[p].active ? 1 : 0;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = cnt;
+}
+
+}  // namespace
+
+struct srj_batch {
+    int device = 0;
+    int nprob = 0;
+    int T = 8;
+    std::vector<srj::BatchProb> probs;   // host copy (f / u filled per solve)
+    std::vector<int> M;
+    int64_t total_points = 0;
+    int ntiles = 0, nrowblocks = 0;
+    srj::BatchProb* d_probs = nullptr;
+    srj::BatchState* d_state = nullptr;
+    int4* d_tiles = nullptr;
+    int2* d_rowblocks = nullptr;
+    float* d_cw = nullptr;
+    float* d_pool = nullptr;  // all FP32 workspaces
+    double* d_partials = nullptr;
+    int* d_count = nullptr;
+    int* h_count = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t phases = nullptr;
+    double graph_tol = -1.0;
+    int graph_max_cycles = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    ~srj_batch() {
+        if (phases) cudaGraphExecDestroy(phases);
+        if (cap) cudaStreamDestroy(cap);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        cudaFree(d_probs); cudaFree(d_state); cudaFree(d_tiles); cudaFree(d_rowblocks);
+        cudaFree(d_cw); cudaFree(d_pool); cudaFree(d_partials); cudaFree(d_count);
+        if (h_count) cudaFreeHost(h_count);
+    }
+};
+
+namespace {
+
+cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles) {
+    const int pb = (b->nprob + kThreads - 1) / kThreads;
+    cudaError_t e = srj::launch_batch_sweep_tb(b->T, (unsigned)b->ntiles, b->d_probs, b->d_state, b->d_tiles, b->d_cw, s);
+    if (e != cudaSuccess) return e;
+    k_batch_advance<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->nprob, b->T);
+    k_batch_update<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 1, 0);
+    k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinCycle, tol,
+                                             max_cycles);
+    return cudaGetLastError();
+}
+
+int capture_phases(srj_batch* b, double tol, int max_cycles) {
+    if (b->phases) { cudaGraphExecDestroy(b->phases); b->phases = nullptr; }
+    cudaGraph_t graph = nullptr;
+    SRJ_BCUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < kPhasesPerGraph && err == cudaSuccess; ++i) err = issue_phase(b, b->cap, tol, max_cycles);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SRJ_BCUDA(err); }
+    SRJ_BCUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&b->phases, graph, 0);
+    cudaGraphDestroy(graph);
+    SRJ_BCUDA(e3);
+    b->graph_tol = tol;
+    b->graph_max_cycles = max_cycles;
+    return SRJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* srj_batch_last_error(void) { return g_batch_err.c_str(); }
+
+int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr, int temporal_depth) {
+    if (!out) return bfail(SRJ_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || nprob > (1 << 20) || !pr) return bfail(SRJ_ERR_INVALID_ARG, "need 1..2^20 problems");
+    if (temporal_depth == 0) temporal_depth = 8;
+    if (temporal_depth < 1 || temporal_depth > srj::tb_max_steps())
+        return bfail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..%d", srj::tb_max_steps());
+    srj_batch* b = new (std::nothrow) srj_batch();
+    if (!b) return bfail(SRJ_ERR_NO_MEMORY, "host allocation failed");
+    auto bail = [&](int code) { delete b; return code; };
+    b->nprob = nprob;
+    b->T = temporal_depth;
+    int TX = 0, TY = 0;
+    srj::tb_tile_shape(b->T, &TX, &TY);
+
+    std::vector<float> cw;
+    std::vector<int4> tiles;
+    std::vector<int2> rowblocks;
+    std::vector<size_t> pool_off;
+    size_t pool_floats = 0;
+    b->probs.resize(nprob);
+    for (int p = 0; p < nprob; ++p) {
+        const srj_batch_problem_t& q = pr[p];
+        if (q.nx < 1 || q.ny < 1 || q.nx > 65536 || q.ny > 65536)
+            return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: dims out of range", p));
+        if (!(q.h > 0.0) || !std::isfinite(q.h)) return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: bad h", p));
+        if (q.P < 1 || q.P > 32 || !q.omega || !q.q) return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: bad schedule", p));
+        std::vector<double> w(q.omega, q.omega + q.P);
+        std::vector<int32_t> qq(q.q, q.q + q.P);
+        int64_t M = 0;
+        for (int i = 0; i < q.P; ++i) {
+            if (!(w[i] > 0.0) || !std::isfinite(w[i]) || qq[i] < 1)
+                return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: bad weight or repetition", p));
+            M += qq[i];
+        }
+        if (M > (1 << 20)) return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: M too large", p));
+        const int64_t dims[2] = {q.nx, q.ny};
+        const double g = srj::host_max_cycle_log10(w, qq, 2, dims);
+        if (!(g < 0.0)) return bail(bfail(SRJ_ERR_BAD_SCHEDULE, "problem %d: integer scheme does not contract (%.3g)", p, g));
+        std::vector<int32_t> order;
+        if (q.order) {
+            order.assign(q.order, q.order + M);
+            std::vector<int64_t> cnt(q.P, 0);
+            for (int32_t v : order) {
+                if (v < 0 || v >= q.P) return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: order out of range", p));
+                cnt[v]++;
+            }
+            for (int i = 0; i < q.P; ++i)
+                if (cnt[i] != qq[i]) return bail(bfail(SRJ_ERR_INVALID_ARG, "problem %d: order does not match q", p));
+        } else {
+            order = srj::host_drift_order(w, qq, srj::host_kappa_min(2, dims));
+        }
+        srj::BatchProb& P = b->probs[p];
+        const srj::Geom geo = srj::make_geom(2, dims);
+        P.nx = (int)q.nx;
+        P.ny = (int)q.ny;
+        P.p32 = geo.p32;
+        P.h2 = q.h * q.h;
+        P.M = (int)M;
+        P.c_off = (int)cw.size();
+        for (int32_t v : order) cw.push_back((float)(w[v] / 4.0));
+        const size_t n32 = (size_t)((geo.n32 + 63) / 64 * 64);
+        pool_off.push_back(pool_floats);
+        pool_floats += 3 * n32;
+        b->M.push_back((int)M);
+        b->total_points += q.nx * q.ny;
+        const int gx = (int)((q.nx + TX - 1) / TX), gy = (int)((q.ny + TY - 1) / TY);
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) tiles.push_back(make_int4(p, bx, by, 0));
+        P.rb_begin = (int)rowblocks.size();
+        for (int y = 1; y <= q.ny; y += kRowsPerBlock) rowblocks.push_back(make_int2(p, y));
+        P.rb_end = (int)rowblocks.size();
+        if (cw.size() > (size_t)1 << 30) return bail(bfail(SRJ_ERR_INVALID_ARG, "weight table too large"));
+    }
+    b->ntiles = (int)tiles.size();
+    b->nrowblocks = (int)rowblocks.size();
+    if (cudaGetDevice(&b->device) != cudaSuccess) return bail(bfail(SRJ_ERR_CUDA, "no CUDA device"));
+    auto alloc = [](void** ptr, size_t by) { return cudaMalloc(ptr, by) == cudaSuccess; };
+    bool ok = alloc((void**)&b->d_pool, sizeof(float) * pool_floats) &&
+              alloc((void**)&b->d_probs, sizeof(srj::BatchProb) * nprob) &&
+              alloc((void**)&b->d_state, sizeof(srj::BatchState) * nprob) &&
+              alloc((void**)&b->d_tiles, sizeof(int4) * tiles.size()) &&
+              alloc((void**)&b->d_rowblocks, sizeof(int2) * rowblocks.size()) &&
+              alloc((void**)&b->d_cw, sizeof(float) * cw.size()) &&
+              alloc((void**)&b->d_partials, sizeof(double) * 2 * rowblocks.size()) &&
+              alloc((void**)&b->d_count, sizeof(int));
+    if (!ok) { cudaGetLastError(); return bail(bfail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
+    for (int p = 0; p < nprob; ++p) {
+        const int64_t dims[2] = {pr[p].nx, pr[p].ny};
+        const size_t n32 = (size_t)((srj::make_geom(2, dims).n32 + 63) / 64 * 64);
+        b->probs[p].ea = b->d_pool + pool_off[p];
+        b->probs[p].eb = b->probs[p].ea + n32;
+        b->probs[p].r32 = b->probs[p].eb + n32;
+        b->probs[p].f = nullptr;
+        b->probs[p].u = nullptr;
+    }
+    if (cudaMemset(b->d_pool, 0, sizeof(float) * pool_floats) != cudaSuccess ||
+        cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_rowblocks, rowblocks.data(), sizeof(int2) * rowblocks.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_cw, cw.data(), sizeof(float) * cw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_count, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        srj::tb_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        return bail(bfail(SRJ_ERR_CUDA, "batch set-up failed"));
+    }
+    *out = b;
+    return SRJ_OK;
+}
+
+int srj_batch_destroy(srj_batch_t b) {
+    if (!b) return SRJ_OK;
+    cudaDeviceSynchronize();
+    delete b;
+    return SRJ_OK;
+}
+
+int srj_batch_info(srj_batch_t b, int64_t* total_points, int64_t* tiles, int* temporal_depth, int64_t* sum_M) {
+    if (!b) return bfail(SRJ_ERR_INVALID_ARG, "batch is NULL");
+    if (total_points) *total_points = b->total_points;
+    if (tiles) *tiles = b->ntiles;
+    if (temporal_depth) *temporal_depth = b->T;
+    if (sum_M) { int64_t s = 0; for (int m : b->M) s += m; *sum_M = s; }
+    return SRJ_OK;
+}
+
+int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, double tol, int64_t max_cycles,
+                    void* stream, srj_stats_t* stats, double* device_ms) {
+    if (!b || !f || !u) return bfail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol >= 0.0) || max_cycles < 0 || max_cycles > (1 << 30))
+        return bfail(SRJ_ERR_INVALID_ARG, "tol must be >= 0 and max_cycles in 0..2^30");
+    int dev = -1;
+    SRJ_BCUDA(cudaGetDevice(&dev));
+    if (dev != b->device) return bfail(SRJ_ERR_INVALID_ARG, "batch was created on device %d", b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int p = 0; p < b->nprob; ++p) {
+        if (!f[p] || !u[p]) return bfail(SRJ_ERR_INVALID_ARG, "problem %d: NULL array", p);
+        b->probs[p].f = f[p];
+        b->probs[p].u = u[p];
+    }
+    std::vector<srj::BatchState> st(b->nprob);
+    for (auto& x : st) {
+        std::memset(&x, 0, sizeof x);
+        x.active = 1;
+        x.cycle_end = 1;
+        x.fresh = 1;
+        x.scale = x.inv_scale = 1.0;
+    }
+    SRJ_BCUDA(cudaMemcpyAsync(b->d_probs, b->probs.data(), sizeof(srj::BatchProb) * b->nprob, cudaMemcpyHostToDevice, s));
+    SRJ_BCUDA(cudaMemcpyAsync(b->d_state, st.data(), sizeof(srj::BatchState) * b->nprob, cudaMemcpyHostToDevice, s));
+    const int pb = (b->nprob + kThreads - 1) / kThreads;
+    const int mc = (int)std::max<int64_t>(max_cycles, 1);
+    // initial residual (norms, then the scaled FP32 defect)
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 0, 1);
+    k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit0, tol, mc);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 1, 1);
+    k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit1, tol, mc);
+    SRJ_BCUDA(cudaGetLastError());
+    if (b->graph_tol != tol || b->graph_max_cycles != mc) {
+        int rc = capture_phases(b, tol, mc);
+        if (rc) return rc;
+    }
+    // Each phase advances every active problem by at least one step, so
+    // sum_p M_p * max_cycles phases bound the loop.
+    int64_t max_phases = 0;
+    for (int m : b->M) max_phases = std::max<int64_t>(max_phases, (int64_t)m);
+    max_phases = max_phases * mc + kPhasesPerGraph;
+    SRJ_BCUDA(cudaEventRecord(b->ev0, s));
+    int64_t phases = 0;
+    if (max_cycles > 0) {
+        for (;;) {
+            SRJ_BCUDA(cudaGraphLaunch(b->phases, s));
+            phases += kPhasesPerGraph;
+            k_batch_count<<<1, kThreads, 0, s>>>(b->d_state, b->nprob, b->d_count);
+            SRJ_BCUDA(cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SRJ_BCUDA(cudaStreamSynchronize(s));
+            if (*b->h_count == 0 || phases >= max_phases) break;
+        }
+    }
+    SRJ_BCUDA(cudaEventRecord(b->ev1, s));
+    SRJ_BCUDA(cudaMemcpyAsync(st.data(), b->d_state, sizeof(srj::BatchState) * b->nprob, cudaMemcpyDeviceToHost, s));
+    SRJ_BCUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    SRJ_BCUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (device_ms) *device_ms = ms;
+    int status = SRJ_OK;
+    for (int p = 0; p < b->nprob; ++p) {
+        const srj::BatchState& x = st[p];
+        int ps = x.active ? SRJ_ERR_NOT_CONVERGED : x.status;
+        if (max_cycles == 0 && x.active) ps = (x.r0 == 0.0) ? SRJ_OK : SRJ_ERR_NOT_CONVERGED;
+        if (stats) {
+            srj_stats_t& o = stats[p];
+            o.cycles = x.cycles;
+            o.sweeps = (int64_t)x.cycles * b->M[p];
+            o.residual_checks = 1 + x.cycles;
+            o.r0_l2 = x.r0;
+            o.res_l2 = x.l2;
+            o.res_linf = x.linf;
+            o.rel_res = x.r0 > 0 ? x.l2 / x.r0 : 0.0;
+            o.sweep_ms = ms;
+        }
+        if (ps != SRJ_OK && status == SRJ_OK) status = ps;
+    }
+    if (status != SRJ_OK) bfail(status, "not every problem converged");
+    return status;
+}
+
+}  // extern "C"

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace srj {
@@ -78,6 +80,44 @@ cudaError_t tb_prepare();  // kernel attributes (dynamic shared memory)
 // rin (pitched float32), writes the interior of eout (eout != ein).
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
                                 const TbSteps& steps, cudaStream_t s);
+
+// ---- batched solver (independent 2-D problems, mixed precision) -----------
+
+// Static per-problem data, in device memory.
+struct BatchProb {
+    int nx, ny;            // interior points
+    int64_t p32;           // float32 row pitch
+    double h2;             // h^2
+    int M;                 // steps per cycle
+    int c_off;             // offset of the problem's weights in the weight table
+    float *ea, *eb, *r32;  // pitched float32 workspaces (ghosts 0)
+    const double* f;       // caller's arrays (set per solve)
+    double* u;
+    int rb_begin, rb_end;  // range of the problem's row blocks (residual partials)
+};
+
+// Dynamic per-problem state, in device memory.
+struct BatchState {
+    int k;          // position in the cycle
+    int cur;        // 0: current correction in ea, 1: in eb
+    int fresh;      // correction is identically 0 (start of a cycle)
+    int active;     // still iterating
+    int cycle_end;  // a cycle has just completed (update / residual due)
+    int cycles;     // completed cycles
+    int status;     // SRJ_OK / NOT_CONVERGED / DIVERGED when inactive
+    int pad;
+    double scale, inv_scale;  // power-of-two scaling of the FP32 defect
+    double r0, l2, linf;
+};
+
+void tb_tile_shape(int T, int* TX, int* TY);
+cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const BatchProb* probs, const BatchState* st,
+                                  const int4* tiles, const float* cw, cudaStream_t s);
+
+// Host-side schedule helpers shared by the plan and the batch (srj_plan.cu).
+std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin);
+double host_max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, int nd, const int64_t* dims);
+double host_kappa_min(int nd, const int64_t* dims);
 
 // grad_g[ghost q] = sum of lambda over the interior neighbours of q; interior 0.
 cudaError_t launch_boundary_adjoint(const Geom& g, const double* lambda, double* grad_g, cudaStream_t s);

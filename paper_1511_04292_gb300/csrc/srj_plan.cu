@@ -146,11 +146,19 @@ std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector
     return order;
 }
 
-struct Stream {
-    cudaStream_t s;
-};
-
 }  // namespace
+
+namespace srj {
+std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
+    return drift_order(w, q, kmin);
+}
+double host_max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, int nd,
+                            const int64_t* dims) {
+    const double kmin = kappa_min_of(nd, dims), kmax = kappa_max_of(nd, dims);
+    return kmin < kmax ? max_cycle_log10(w, q, kmin, kmax) : cycle_log10(w, q, kmin);
+}
+double host_kappa_min(int nd, const int64_t* dims) { return kappa_min_of(nd, dims); }
+}  // namespace srj
 
 struct srj_plan {
     int device = 0;

@@ -39,13 +39,14 @@ __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) 
 // slot, so each step costs one barrier and four shared-memory accesses per lane.
 template <int T, bool MASKED>
 __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr)[kBand], float4* xch,
-                                           const TbSteps& steps, int lane, int w, const bool (&inx)[4],
+                                           const float (&cs)[8], int n, int lane, int w, const bool (&inx)[4],
                                            const bool (&iny)[kBand]) {
     const float two_d = 4.0f;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        const float c = steps.c[t];
+        if (t >= n) break;  // n is uniform over the block
+        const float c = cs[t];
         float4* slot = xch + (t & 1) * (2 * kWarps * 32);
         slot[(2 * w) * 32 + lane] = e[0];              // top row of this band
         slot[(2 * w + 1) * 32 + lane] = e[kBand - 1];  // bottom row
@@ -78,26 +79,28 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
     }
 }
 
+// One tile of T-step blocking on one grid: n <= T steps with weights cs[0..n).
+// X0 / Y0: padded coordinates of the tile's first column / row.  fresh: the
+// input iterate is identically zero (start of a defect-correction cycle), so it
+// is not read.
 template <int T>
-__global__ void __launch_bounds__(kWarps * 32, 2)
-k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
-               TbSteps steps) {
+__device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const float* __restrict__ rin,
+                                           float* __restrict__ eout, int nx, int ny, int64_t p32, int64_t rows,
+                                           const float (&cs)[8], int n, int bx, int by, bool fresh, float4* xch) {
     constexpr int HX = T <= 4 ? 4 : 8;
     constexpr int TX = kSX - 2 * HX;
     constexpr int TY = kSY - 2 * T;
-    __shared__ float4 xch[2 * 2 * kWarps * 32];  // [slot][warp][top/bottom][lane]
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int X0 = 1 + TX * (int)blockIdx.x - HX;  // padded x of tile column 0
-    const int Y0 = 1 + TY * (int)blockIdx.y - T;   // padded y of tile row 0
+    const int X0 = 1 + TX * bx - HX;
+    const int Y0 = 1 + TY * by - T;
 
     // Band fill: float4 loads of e and r straight into registers.  The float32
     // column of padded x is x + 3, a multiple of 4 here, so each float4 lies
     // wholly inside or outside the buffer (rows 0..rows-1, columns 0..p32-1);
     // outside ones read as zero.
-    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
     const int col = X0 + 3 + 4 * lane;
-    const bool colok = col >= 0 && col + 4 <= g.p32;
+    const bool colok = col >= 0 && col + 4 <= p32;
     float4 e[kBand], rr[kBand];
     bool iny[kBand];
 #pragma unroll
@@ -106,22 +109,22 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
         e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         rr[i] = e[i];
         if (colok && y >= 0 && y < rows) {
-            const int64_t off = y * g.p32 + col;
-            e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+            const int64_t off = y * p32 + col;
+            if (!fresh) e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
             rr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
         }
-        iny[i] = y >= 1 && y <= g.ny;
+        iny[i] = y >= 1 && y <= ny;
     }
     bool inx[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int x = X0 + 4 * lane + j;
-        inx[j] = x >= 1 && x <= g.nx;
+        inx[j] = x >= 1 && x <= nx;
     }
     // tiles whose every point is an interior grid point need no masking
-    const bool interior = X0 >= 1 && X0 + kSX - 1 <= g.nx && Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
-    if (interior) band_steps<T, false>(e, rr, xch, steps, lane, w, inx, iny);
-    else          band_steps<T, true>(e, rr, xch, steps, lane, w, inx, iny);
+    const bool interior = X0 >= 1 && X0 + kSX - 1 <= nx && Y0 >= 1 && Y0 + kSY - 1 <= ny;
+    if (interior) band_steps<T, false>(e, rr, xch, cs, n, lane, w, inx, iny);
+    else          band_steps<T, true>(e, rr, xch, cs, n, lane, w, inx, iny);
 
     // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
@@ -131,9 +134,9 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
         const int row = w * kBand + i;
         if (row < T || row >= T + TY) continue;
         const int y = Y0 + row;
-        if (y < 1 || y > g.ny) continue;
+        if (y < 1 || y > ny) continue;
         const int x = X0 + 4 * lane;
-        float* dst = eout + (int64_t)y * g.p32 + x + 3;  // 16-byte aligned
+        float* dst = eout + (int64_t)y * p32 + x + 3;  // 16-byte aligned
         if (inx[0] && inx[3]) {
             *reinterpret_cast<float4*>(dst) = e[i];
         } else {
@@ -143,6 +146,39 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
             if (inx[3]) dst[3] = e[i].w;
         }
     }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
+               TbSteps steps) {
+    __shared__ float4 xch[2 * 2 * kWarps * 32];  // [slot][warp][top/bottom][lane]
+    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
+    tile_sweep<T>(ein, rin, eout, g.nx, g.ny, g.p32, rows, steps.c, steps.T, (int)blockIdx.x, (int)blockIdx.y,
+                  false, xch);
+}
+
+// Batched form: one launch covers the tiles of every problem of a batch; each
+// block finds its problem in the tile table and advances it by
+// n = min(T, M - k) steps of its own cycle order.  Problems that have finished
+// are skipped.
+template <int T>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_batch_sweep_tb(const BatchProb* __restrict__ probs, const BatchState* __restrict__ st,
+                 const int4* __restrict__ tiles, const float* __restrict__ cw) {
+    __shared__ float4 xch[2 * 2 * kWarps * 32];
+    const int4 tl = tiles[blockIdx.x];
+    const int p = tl.x;
+    const BatchState s = st[p];
+    if (!s.active) return;
+    const BatchProb P = probs[p];
+    const int n = min(T, P.M - s.k);
+    float cs[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) cs[t] = (t < n) ? cw[P.c_off + s.k + t] : 0.f;
+    const float* ein = s.cur ? P.eb : P.ea;
+    float* eout = s.cur ? P.ea : P.eb;
+    tile_sweep<T>(ein, P.r32, eout, P.nx, P.ny, P.p32, (int64_t)P.ny + 2, cs, n, tl.y, tl.z, s.fresh != 0, xch);
 }
 
 size_t smem_bytes() { return 0; }
@@ -160,6 +196,12 @@ template <int T>
 void launch_T(dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
               const TbSteps& st) {
     k_sweep_f32_tb<T><<<grd, kWarps * 32, smem_bytes(), s>>>(ein, rin, eout, g, st);
+}
+
+template <int T>
+void launch_batch_T(unsigned ntiles, cudaStream_t s, const BatchProb* probs, const BatchState* st, const int4* tiles,
+                    const float* cw) {
+    k_batch_sweep_tb<T><<<ntiles, kWarps * 32, 0, s>>>(probs, st, tiles, cw);
 }
 
 cudaError_t tb_prepare() {
@@ -190,6 +232,28 @@ cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* ri
         case 6: launch_T<6>(grd, s, me, mr, eout, g, steps); break;
         case 7: launch_T<7>(grd, s, me, mr, eout, g, steps); break;
         default: launch_T<8>(grd, s, me, mr, eout, g, steps); break;
+    }
+    return cudaGetLastError();
+}
+
+void tb_tile_shape(int T, int* TX, int* TY) {
+    const int HX = T <= 4 ? 4 : 8;
+    *TX = kSX - 2 * HX;
+    *TY = kSY - 2 * T;
+}
+
+cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const BatchProb* probs, const BatchState* st,
+                                  const int4* tiles, const float* cw, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    switch (T) {
+        case 1: launch_batch_T<1>(ntiles, s, probs, st, tiles, cw); break;
+        case 2: launch_batch_T<2>(ntiles, s, probs, st, tiles, cw); break;
+        case 3: launch_batch_T<3>(ntiles, s, probs, st, tiles, cw); break;
+        case 4: launch_batch_T<4>(ntiles, s, probs, st, tiles, cw); break;
+        case 5: launch_batch_T<5>(ntiles, s, probs, st, tiles, cw); break;
+        case 6: launch_batch_T<6>(ntiles, s, probs, st, tiles, cw); break;
+        case 7: launch_batch_T<7>(ntiles, s, probs, st, tiles, cw); break;
+        default: launch_batch_T<8>(ntiles, s, probs, st, tiles, cw); break;
     }
     return cudaGetLastError();
 }
