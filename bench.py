@@ -51,6 +51,8 @@ def parse():
                     help="cycles of the plain FP64 comparator to time (0 = run it to tolerance)")
     ap.add_argument("--cpu-sweeps", type=int, default=4, help="oracle sweeps in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 3-D 512^3 and batched secondary measurements")
     ap.add_argument("--kernel-case", choices=["f32", "f64"], default=None,
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
@@ -149,6 +151,54 @@ def workload_config(args):
             "rhs": "seeded N(0,1) field, 5x5 box mean (seed %d); Dirichlet data: seeded cubic polynomial" % SEED_F,
             "step": "one full solve from u0 to tolerance",
             "l2": "flushed between timed steps (256 MiB write); per-sweep working set ~134 MB ~ L2 size"}
+
+
+def secondary_workloads(stream):
+    """One timed solve each of the 3-D workload and of the batched workload."""
+    import numpy as np
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
+    out = {}
+    # 3-D: 512^3 interior, 8 Gaussian blobs, mixed precision, P = 12, tol 1e-9
+    n = 512
+    f_h, u0_h = W.gaussian_blobs_3d(n, 3)
+    f = torch.from_numpy(f_h).cuda(); u0 = torch.from_numpy(u0_h).cuda(); u = torch.empty_like(u0)
+    del f_h, u0_h
+    plan = srj.Plan.from_table((n, n, n), 12, "mixed")
+    u.copy_(u0); plan.solve(f, u, 1e-9, 200)  # warm-up
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    u.copy_(u0); torch.cuda.synchronize()
+    a.record(stream); st = plan.solve(f, u, 1e-9, 200); b.record(stream); torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out["3d_poisson_512^3_P12_mixed_tol1e-9"] = {
+        "time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * n ** 3 / (ms / 1e3) / 1e9,
+        "cycles": st["cycles"], "final_rel_residual": st["rel_res"], "sweep_kernel": "k_sweep_f32<3> (unblocked)",
+        "sweep_kernel_gbs": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
+    del f, u0, u, plan
+    torch.cuda.empty_cache()
+    # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10
+    specs = W.batch_specs()
+    probs, fs, u0s = [], [], []
+    for nn, P, seed in specs:
+        row = srj.schedules.lookup(2, nn, P)
+        fh, uh = W.random_smooth_problem_2d(nn, seed)
+        probs.append(dict(dims=(nn, nn), h=1.0 / (nn + 1), omega=row["omega"], q=row["q"], order=row["order"]))
+        fs.append(torch.from_numpy(fh).cuda()); u0s.append(torch.from_numpy(uh).cuda())
+    batch = srj.Batch(probs)
+    us = [x.clone() for x in u0s]
+    batch.solve(fs, us, 1e-10, 500)  # warm-up
+    us = [x.clone() for x in u0s]
+    torch.cuda.synchronize()
+    a.record(stream); stats, dms, rc = batch.solve(fs, us, 1e-10, 500); b.record(stream); torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    upd = sum(s_["sweeps"] * nn * nn for s_, (nn, _, _) in zip(stats, specs))
+    out["batched_256_problems_n64-1024_P5-10_mixed_tol1e-10"] = {
+        "time_to_tol_s": ms / 1e3, "gupdates_per_s": upd / (ms / 1e3) / 1e9, "status": rc,
+        "max_cycles": max(s_["cycles"] for s_ in stats), "points": sum(nn * nn for nn, _, _ in specs),
+        "temporal_depth": batch.info()["temporal_depth"],
+        "max_final_rel_residual": max(s_["rel_res"] for s_ in stats)}
+    return out
 
 
 def oracle_sample(args):
@@ -311,6 +361,12 @@ def run_srj(args):
                "sample": "%d FP64 oracle sweeps of the full %dx%d grid (%.1f s)" % (args.cpu_sweeps, n, n, dt),
                "host_cores_total": os.cpu_count()}
 
+    secondary = None
+    if rank == 0 and not args.no_secondary:
+        del p64
+        torch.cuda.empty_cache()
+        secondary = secondary_workloads(stream)
+
     launches_per_step = 2 + stats[-1]["cycles"] * (launches_per_cycle + 2)
     line = {"metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -321,7 +377,7 @@ def run_srj(args):
             "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Gupdates/s", "h2d_bytes_per_step": 2 * f_h.nbytes,
                     "d2h_bytes_per_step": u0_h.nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
-            "gpu_launches": launches_per_step * args.steps}
+            "gpu_launches": launches_per_step * args.steps, "secondary_workloads": secondary}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -245,6 +245,23 @@ int srj_batch_solve(srj_batch_t batch, const double *const *f, double *const *u,
 /* Text of the last batch error on the calling thread. */
 const char *srj_batch_last_error(void);
 
+/*
+ * srj_gradient -- backward pass of u = S(f, g), the solution of A_h u = h^2 f + B g
+ * (B: ghost neighbours), for a scalar loss L(u).  Given grad_u = dL/du (device,
+ * padded; its ghost layer is dL/dg through u's own ghost layer, which equals g):
+ *   lambda solves A_h lambda = grad_u on the interior (A_h is symmetric, so the
+ *   adjoint solve is the same SRJ solve) with lambda = 0 on the ghost layer;
+ *   grad_f = h^2 lambda on the interior (0 on the ghosts);
+ *   grad_g = B^T lambda + grad_u on the ghost layer (0 inside), B^T lambda being
+ *   the sum of lambda over each ghost point's interior neighbours.
+ * lambda is in/out: its interior is the initial guess (0 is fine), its ghost
+ * layer is set to 0.  The solve uses the plan's schedule and precision, runs to
+ * tol / max_cycles like srj_solve and fills stats.  Returns the solve's status
+ * (outputs are written for SRJ_OK and SRJ_ERR_NOT_CONVERGED).
+ */
+int srj_gradient(srj_plan_t plan, const double *grad_u, double *lambda, double *grad_f, double *grad_g, double tol,
+                 int64_t max_cycles, void *stream, srj_stats_t *stats);
+
 /* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 

@@ -62,6 +62,8 @@ def make_rows(grids=GRIDS, log=print):
             window, suffix = S.window_growth(omega, order, km)
             if not gmax < 0.0:
                 raise S.ScheduleError("integer scheme does not contract: P=%d n=%d" % (P, n))
+            if window > np.log10(2 * omega[0]) + 1.5:
+                raise S.ScheduleError("cycle order grows too much inside the cycle: P=%d n=%d" % (P, n))
             rows.append(dict(
                 ndim=ndim, n=n, P=P,
                 kappa_min=km, n_eff=neff_dirichlet([n + 1] * ndim),

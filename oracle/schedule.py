@@ -275,11 +275,10 @@ def max_cycle_factor(omega, q, kappa_m, kappa_max=KAPPA_MAX, samples=20001):
 # Cycle ordering
 # ---------------------------------------------------------------------------
 
-def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, samples=2000):
+def _order_drift_once(omega, q, kappa_m, kappa_max, samples):
     """Order of the M weight applications inside one cycle.
 
-    Sect. 5.1 notes that the largest over-relaxations must be spread over the
-    cycle (an even distribution avoids overflow) but gives no algorithm.  In
+    One greedy pass on one sampling grid (see ``order_drift``).  In
     floating point what matters is how far the partial products of the
     amplification factors stray inside the cycle: a rounding error made at one
     step is multiplied by the product of the factors that follow it.  This
@@ -314,6 +313,34 @@ def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, samples=2000):
         left[best_i] -= 1
         cur += L[best_i]
     return order
+
+
+DRIFT_GRIDS = (1000, 2000, 3000, 4000)
+
+
+def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, grids=DRIFT_GRIDS):
+    """Order of the M weight applications inside one cycle.
+
+    Sect. 5.1 notes that the largest over-relaxations must be spread over the
+    cycle (an even distribution avoids overflow) but gives no algorithm.  In
+    floating point what matters is how far the partial products of the
+    amplification factors stray inside the cycle: a rounding error made at one
+    step is multiplied by the product of the factors that follow it.  The
+    greedy pass (``_order_drift_once``) keeps, for every sampled kappa, the
+    running log-product close to the straight line from 0 to the full-cycle
+    value.  The greedy is sensitive to the sampling grid (on some schedules one
+    grid leaves a cluster of large weights late in the cycle), so the pass is
+    run on geometric grids of each size in `grids` and the order with the
+    smallest worst-window growth (then suffix growth) on a 4001-point grid is
+    kept.  Returns level indices (0-based) of length M.
+    """
+    best = None
+    for n in grids:
+        o = _order_drift_once(omega, q, kappa_m, kappa_max, n)
+        key = window_growth(omega, o, kappa_m, kappa_max, samples=4001)
+        if best is None or key < best[0]:
+            best = (key, o)
+    return best[1]
 
 
 def window_growth(omega, order, kappa_m, kappa_max=KAPPA_MAX, samples=2000):

@@ -108,6 +108,7 @@ SIGNATURES = {
     "srj_steps": (_I, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "srj_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),
     "srj_boundary_adjoint": (_I, [_VP, _VP, _VP, _VP]),
+    "srj_gradient": (_I, [_VP, _VP, _VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
     "srj_kappa_min": (_I, [_I, _I64P, _DP]),
     "srj_schedule_check": (_I, [_I, _DP, _I32P, _D, _D, _DP]),
     "srj_schedule_order": (_I, [_I, _DP, _I32P, _D, _I32P]),

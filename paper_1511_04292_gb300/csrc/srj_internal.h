@@ -119,6 +119,13 @@ std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::v
 double host_max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, int nd, const int64_t* dims);
 double host_kappa_min(int nd, const int64_t* dims);
 
+// Set the ghost layer of a padded float64 grid to 0.
+cudaError_t launch_zero_ghosts(const Geom& g, double* a, cudaStream_t s);
+// grad_f = h2 * lambda (interior; ghosts 0); grad_g = B^T lambda + grad_u on the
+// ghost layer (interior 0).
+cudaError_t launch_adjoint_finish(const Geom& g, double h2, const double* lambda, const double* grad_u,
+                                  double* grad_f, double* grad_g, cudaStream_t s);
+
 // grad_g[ghost q] = sum of lambda over the interior neighbours of q; interior 0.
 cudaError_t launch_boundary_adjoint(const Geom& g, const double* lambda, double* grad_g, cudaStream_t s);
 

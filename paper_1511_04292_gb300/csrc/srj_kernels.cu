@@ -263,6 +263,44 @@ __global__ void k_boundary_adjoint(Geom g, const double* __restrict__ lam, doubl
     }
 }
 
+__device__ inline double ghost_adjoint(const Geom& g, const double* __restrict__ lam, int x, int y, int z) {
+    // interior neighbours of a ghost point: at most one per axis direction
+    double acc = 0.0;
+    const int c[3] = {x, y, z};
+    const int hi[3] = {g.nx, g.ny, g.nz};
+    for (int ax = 0; ax < g.nd; ++ax) {
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int n[3] = {c[0], c[1], c[2]};
+            n[ax] += sgn;
+            bool inner = true;
+            for (int a = 0; a < g.nd; ++a) inner = inner && n[a] >= 1 && n[a] <= hi[a];
+            if (inner) acc += lam[idx64(g, n[0], n[1], g.nd == 3 ? n[2] : 0)];
+        }
+    }
+    return acc;
+}
+
+__global__ void k_zero_ghosts(Geom g, double* __restrict__ a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n64; i += (int64_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (!decode(g, i, x, y, z)) a[i] = 0.0;
+    }
+}
+
+__global__ void k_adjoint_finish(Geom g, double h2, const double* __restrict__ lam, const double* __restrict__ gu,
+                                 double* __restrict__ gf, double* __restrict__ gg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n64; i += (int64_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (decode(g, i, x, y, z)) {
+            gf[i] = h2 * lam[i];
+            gg[i] = 0.0;
+        } else {
+            gf[i] = 0.0;
+            gg[i] = ghost_adjoint(g, lam, x, y, z) + gu[i];
+        }
+    }
+}
+
 inline int grid_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
     if (b > 152 * 16) b = 152 * 16;
@@ -337,6 +375,17 @@ cudaError_t launch_source_f32(const Geom& g, double h2, const double* f, float* 
 
 cudaError_t launch_from_f32(const Geom& g, const float* e, double* u, cudaStream_t s) {
     k_from_f32<<<grid_for(g.n64), kThreads, 0, s>>>(g, e, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_ghosts(const Geom& g, double* a, cudaStream_t s) {
+    k_zero_ghosts<<<grid_for(g.n64), kThreads, 0, s>>>(g, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_finish(const Geom& g, double h2, const double* lambda, const double* grad_u,
+                                  double* grad_f, double* grad_g, cudaStream_t s) {
+    k_adjoint_finish<<<grid_for(g.n64), kThreads, 0, s>>>(g, h2, lambda, grad_u, grad_f, grad_g);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kMaxLevels = 32;
 constexpr int64_t kMaxM = int64_t(1) << 20;
-constexpr int kOrderSamples = 2000;
+constexpr double kMaxSuffixGrowthFP32 = 6.0;  // log10: FP32 rounding x 1e6 ~ 6e-2 relative per cycle
 constexpr int kCheckSamples = 20001;
 
 // Largest eigenvalue of D^-1 A on the Dirichlet grid: (2/d) sum_i cos^2(pi / 2(n_i+1)) < 2.
@@ -112,9 +112,9 @@ double max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>&
 // of the steps after it, so large excursions cost accuracy; Sect. 5.1 asks for
 // the large over-relaxations to be spread over the cycle).  Greedy: at step s
 // take the level with repetitions left that minimises the largest deviation.
-std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
+std::vector<int32_t> drift_order_once(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin,
+                                      int K) {
     const int P = (int)w.size();
-    const int K = kOrderSamples;
     int64_t M = 0;
     for (int v : q) M += v;
     std::vector<double> L((size_t)P * K), total(K, 0.0), cur(K, 0.0);
@@ -148,6 +148,59 @@ std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector
 
 }  // namespace
 
+
+
+// Largest log10 growth of a contiguous run of steps (window) and of a cycle
+// suffix, max over a geometric kappa grid on [kmin, 2].
+void order_growth(const std::vector<double>& w, const std::vector<int32_t>& order, double kmin, int K,
+                  double* window, double* suffix) {
+    const int P = (int)w.size();
+    std::vector<double> L((size_t)P * K);
+    const double lr = std::log(2.0 / kmin);
+    for (int j = 0; j < K; ++j) {
+        const double k = kmin * std::exp(lr * j / (K - 1));
+        for (int i = 0; i < P; ++i) L[(size_t)i * K + j] = std::log10(std::fabs(1.0 - w[i] * k));
+    }
+    std::vector<double> pre(K, 0.0), lo(K, 0.0), mx_pre(K, 0.0);
+    double wmax = 0.0;
+    for (int32_t lev : order) {
+        const double* Li = &L[(size_t)lev * K];
+        for (int j = 0; j < K; ++j) {
+            pre[j] += Li[j];
+            wmax = std::max(wmax, pre[j] - lo[j]);
+            lo[j] = std::min(lo[j], pre[j]);
+            mx_pre[j] = std::max(mx_pre[j], pre[j]);
+        }
+    }
+    // suffix from step a = total - prefix(a); max over a of (total - min prefix)
+    std::vector<double> minpre(K, 0.0), run(K, 0.0);
+    double smax = -INFINITY;
+    for (size_t s = 0; s < order.size(); ++s) {
+        const double* Li = &L[(size_t)order[s] * K];
+        for (int j = 0; j < K; ++j) {
+            smax = std::max(smax, pre[j] - run[j]);  // suffix starting at step s
+            run[j] += Li[j];
+        }
+    }
+    *window = wmax;
+    *suffix = smax;
+}
+
+// The greedy pass depends on its sampling grid; run it on a few grids and keep
+// the order with the smallest worst-window growth (then suffix growth).
+std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
+    const int grids[4] = {1000, 2000, 3000, 4000};
+    std::vector<int32_t> best;
+    double bw = INFINITY, bs = INFINITY;
+    for (int K : grids) {
+        std::vector<int32_t> o = drift_order_once(w, q, kmin, K);
+        double wg, sg;
+        order_growth(w, o, kmin, 4001, &wg, &sg);
+        if (wg < bw || (wg == bw && sg < bs)) { bw = wg; bs = sg; best.swap(o); }
+    }
+    return best;
+}
+
 namespace srj {
 std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
     return drift_order(w, q, kmin);
@@ -171,6 +224,7 @@ struct srj_plan {
     int64_t M = 0;
     std::vector<double> c64;  // omega_k / 2d per step, in cycle order
     double kappa_min = 0, kappa_max = 2, gmax = 0;
+    double order_suffix_growth = 0;
 
     // FP64 workspaces: two iterates and b = h^2 f
     double *ua = nullptr, *ub = nullptr, *b = nullptr;
@@ -394,6 +448,15 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
     } else {
         p->order = drift_order(p->omega, p->q, p->kappa_min);
     }
+    if (precision == SRJ_PREC_MIXED) {
+        double wg = 0, sg = 0;
+        order_growth(p->omega, p->order, p->kappa_min, 4001, &wg, &sg);
+        p->order_suffix_growth = sg;
+        if (sg > kMaxSuffixGrowthFP32)
+            return bail(fail(SRJ_ERR_BAD_SCHEDULE,
+                             "cycle order amplifies FP32 rounding by 10^%.1f inside a cycle (limit 10^%.0f); "
+                             "use another order or FP64", sg, kMaxSuffixGrowthFP32));
+    }
     p->c64.resize((size_t)M);
     for (int64_t k = 0; k < M; ++k) p->c64[(size_t)k] = p->omega[p->order[(size_t)k]] / (double)(2 * ndim);
 
@@ -565,10 +628,35 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
     return SRJ_OK;
 }
 
+static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, double tol, int64_t max_cycles,
+                      void* stream, srj_stats_t* stats);
+
 int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_cycles, void* stream,
               srj_stats_t* stats) {
     int rc = check_plan(p);
     if (rc) return rc;
+    return solve_impl(p, f, p->h2, u, tol, max_cycles, stream, stats);
+}
+
+int srj_gradient(srj_plan_t p, const double* grad_u, double* lambda, double* grad_f, double* grad_g, double tol,
+                 int64_t max_cycles, void* stream, srj_stats_t* stats) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!grad_u || !lambda || !grad_f || !grad_g) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    // A is symmetric: lambda solves A lambda = dL/du (interior) with zero ghosts;
+    // the right-hand side is passed as the source with h^2 replaced by 1.
+    SRJ_CUDA(srj::launch_zero_ghosts(p->g, lambda, s));
+    rc = solve_impl(p, grad_u, 1.0, lambda, tol, max_cycles, stream, stats);
+    if (rc != SRJ_OK && rc != SRJ_ERR_NOT_CONVERGED) return rc;
+    SRJ_CUDA(srj::launch_adjoint_finish(p->g, p->h2, lambda, grad_u, grad_f, grad_g, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, double tol, int64_t max_cycles,
+                      void* stream, srj_stats_t* stats) {
+    int rc = SRJ_OK;
     if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
     if (!(tol >= 0.0) || max_cycles < 0) return fail(SRJ_ERR_INVALID_ARG, "tol must be >= 0 and max_cycles >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -581,12 +669,12 @@ int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_
     if (p->precision == SRJ_PREC_FP64) {
         SRJ_CUDA(cudaMemcpyAsync(p->ua, u, by64, cudaMemcpyDeviceToDevice, s));
         SRJ_CUDA(cudaMemcpyAsync(p->ub, u, by64, cudaMemcpyDeviceToDevice, s));
-        SRJ_CUDA(srj::launch_scale_source(p->g, p->h2, f, p->b, s));
+        SRJ_CUDA(srj::launch_scale_source(p->g, h2, f, p->b, s));
         SRJ_CUDA(srj::launch_residual(p->g, p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s));
     } else {
         const size_t by32 = sizeof(float) * (size_t)p->g.n32;
         SRJ_CUDA(cudaMemsetAsync(p->eb, 0, by32, s));  // ghosts of the corrections are 0
-        SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, nullptr, 1.0, p->ns, s));
+        SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, nullptr, 1.0, p->ns, s));
     }
     if ((rc = read_norms(p, s, &l2, &linf))) return rc;
     st.residual_checks = 1;
@@ -603,7 +691,7 @@ int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_
             int ex = 0;
             std::frexp(linf, &ex);
             scale = std::ldexp(1.0, -ex);
-            SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, p->r32, scale, p->ns, s));
+            SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s));
         }
         for (int64_t c = 0; c < max_cycles; ++c) {
             SRJ_CUDA(cudaEventRecord(p->ev0, s));
@@ -616,7 +704,7 @@ int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_
                 SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[0], s));
                 SRJ_CUDA(cudaEventRecord(p->ev1, s));
                 SRJ_CUDA(srj::launch_update(p->g, u, p->e_final, 1.0 / scale, s));
-                SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, nullptr, p->r32, scale, p->ns, s));
+                SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s));
             }
             if ((rc = read_norms(p, s, &l2, &linf))) return rc;
             float ms = 0.f;
