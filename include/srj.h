@@ -78,6 +78,10 @@ typedef struct srj_stats {
     double  rel_res;         /* res_l2 / r0_l2 (0 if r0_l2 == 0)                   */
     double  sweep_ms;        /* device time of the M-cycle sweep graphs, summed over
                                 cycles (CUDA events on `stream`)                   */
+    int32_t stagnated;       /* 1 if the solve stopped because the residual had not
+                                halved its best value for 4 cycles (floating-point
+                                floor reached before tol); status NOT_CONVERGED  */
+    int32_t reserved;
 } srj_stats_t;
 
 /*
@@ -150,8 +154,11 @@ int srj_plan_order(srj_plan_t plan, int32_t *order_out);
  *   tol    relative tolerance (>= 0).   max_cycles >= 0.
  *   stats  host pointer or NULL.
  * Returns SRJ_OK when converged, SRJ_ERR_NOT_CONVERGED or SRJ_ERR_DIVERGED
- * otherwise (u then holds the last iterate and stats are filled).  Blocks the
- * host until the solve ends; all device work is on `stream`.
+ * otherwise (u then holds the last iterate and stats are filled).  The solve
+ * also stops with SRJ_ERR_NOT_CONVERGED (stats->stagnated = 1) when 4
+ * consecutive cycles fail to halve the smallest residual seen so far: the
+ * residual has reached its floating-point floor above tol.  Blocks the host
+ * until the solve ends; all device work is on `stream`.
  */
 int srj_solve(srj_plan_t plan, const double *f, double *u, double tol, int64_t max_cycles,
               void *stream, srj_stats_t *stats);

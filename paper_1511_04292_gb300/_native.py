@@ -79,7 +79,8 @@ STATUS = {0: "SRJ_OK", -1: "SRJ_ERR_INVALID_ARG", -2: "SRJ_ERR_BAD_SCHEDULE", -3
 class Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("residual_checks", ctypes.c_int64),
                 ("r0_l2", ctypes.c_double), ("res_l2", ctypes.c_double), ("res_linf", ctypes.c_double),
-                ("rel_res", ctypes.c_double), ("sweep_ms", ctypes.c_double)]
+                ("rel_res", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("stagnated", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

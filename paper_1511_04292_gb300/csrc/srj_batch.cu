@@ -149,6 +149,8 @@ __global__ void k_batch_finalize(const srj::BatchProb* __restrict__ probs, srj::
     s.linf = (a == a) ? m : a;
     if (mode == kFinInit0) {
         s.r0 = l2;
+        s.best = l2;
+        s.stall = 0;
         if (!isfinite(l2)) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
         else if (l2 == 0.0 || !(tol < 1.0)) { s.status = SRJ_OK; s.active = 0; }
         else {
@@ -165,7 +167,12 @@ __global__ void k_batch_finalize(const srj::BatchProb* __restrict__ probs, srj::
     if (!isfinite(l2) || l2 > 1e6 * s.r0) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
     else if (l2 / s.r0 <= tol) { s.status = SRJ_OK; s.active = 0; }
     else if (s.cycles >= max_cycles) { s.status = SRJ_ERR_NOT_CONVERGED; s.active = 0; }
-    else { s.k = 0; s.fresh = 1; }
+    else if (!(l2 < 0.5 * s.best) && ++s.stall >= 4) {  // floating-point floor reached
+        s.status = SRJ_ERR_NOT_CONVERGED; s.stagnated = 1; s.active = 0;
+    } else {
+        if (l2 < 0.5 * s.best) { s.best = l2; s.stall = 0; }
+        s.k = 0; s.fresh = 1;
+    }
     st[p] = s;
 }
 
@@ -454,6 +461,8 @@ int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, dou
             o.res_linf = x.linf;
             o.rel_res = x.r0 > 0 ? x.l2 / x.r0 : 0.0;
             o.sweep_ms = ms;
+            o.stagnated = x.stagnated;
+            o.reserved = 0;
         }
         if (ps != SRJ_OK && status == SRJ_OK) status = ps;
     }

@@ -105,9 +105,11 @@ struct BatchState {
     int cycle_end;  // a cycle has just completed (update / residual due)
     int cycles;     // completed cycles
     int status;     // SRJ_OK / NOT_CONVERGED / DIVERGED when inactive
-    int pad;
+    int stall;      // cycles since the residual last halved its best value
+    double best;    // smallest residual norm so far
     double scale, inv_scale;  // power-of-two scaling of the FP32 defect
     double r0, l2, linf;
+    int stagnated, pad2;
 };
 
 void tb_tile_shape(int T, int* TX, int* TY);

@@ -693,6 +693,8 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
             scale = std::ldexp(1.0, -ex);
             SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s));
         }
+        double best = st.r0_l2;
+        int stall = 0;
         for (int64_t c = 0; c < max_cycles; ++c) {
             SRJ_CUDA(cudaEventRecord(p->ev0, s));
             if (p->precision == SRJ_PREC_FP64) {
@@ -721,8 +723,15 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
                 break;
             }
             if (st.rel_res <= tol) { status = SRJ_OK; break; }
+            if (l2 < 0.5 * best) { best = l2; stall = 0; }
+            else if (++stall >= 4) {
+                st.stagnated = 1;
+                status = fail(SRJ_ERR_NOT_CONVERGED, "residual stagnated at rel %.3g after %lld cycles (tol %.3g)",
+                              st.rel_res, (long long)(c + 1), tol);
+                break;
+            }
         }
-        if (status == SRJ_ERR_NOT_CONVERGED)
+        if (status == SRJ_ERR_NOT_CONVERGED && !st.stagnated)
             fail(SRJ_ERR_NOT_CONVERGED, "not converged after %lld cycles (rel %.3g)", (long long)max_cycles, st.rel_res);
     }
     if (p->precision == SRJ_PREC_FP64 && st.cycles > 0)

@@ -104,3 +104,11 @@ def test_full_batched_workload_converges():
         r0, _ = oracle.residual(pr["dims"], pr["h"], f, u0)
         l2, _ = oracle.residual(pr["dims"], pr["h"], f, u.cpu().numpy())
         assert l2 <= 1e-10 * r0 * (1 + 1e-9)
+
+
+def test_batch_stagnation_flag():
+    pr, f, u0 = _problem(128, 6, 2)
+    batch = srj.Batch([pr, pr], temporal_depth=6)
+    ud = [torch.from_numpy(u0).cuda() for _ in range(2)]
+    stats, ms, rc = batch.solve([torch.from_numpy(f).cuda()] * 2, ud, 1e-30, 10000, raise_on_fail=False)
+    assert rc == -3 and all(s["stagnated"] == 1 and s["cycles"] < 200 and s["rel_res"] < 1e-11 for s in stats)

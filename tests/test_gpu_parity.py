@@ -156,6 +156,19 @@ def test_mixed_solve_reaches_tolerance(case):
     assert math.isclose(st["rel_res"], l2 / r0, rel_tol=1e-6, abs_tol=1e-13)
 
 
+def test_stagnation_stops_at_the_floating_point_floor():
+    """A tolerance below the FP64 floor of the residual stops after a few
+    non-improving cycles with NOT_CONVERGED and the stagnated flag, instead of
+    running max_cycles."""
+    n = 256
+    f, u0 = W.random_smooth_problem_2d(n, 4)
+    for prec in ("fp64", "mixed"):
+        plan = srj.Plan.from_table((n, n), 6, prec)
+        st = plan.solve(dev(f), dev(u0), 1e-30, 10000, raise_on_fail=False)
+        assert st["status"] == -3 and st["stagnated"] == 1 and st["cycles"] < 200, st
+        assert st["rel_res"] < 1e-11
+
+
 def test_zero_problem_converges_immediately():
     dims = (16, 16)
     plan = srj.Plan.from_table((64, 64), 5, "mixed")
