@@ -294,11 +294,8 @@ def run_srj(args):
     total_ms = sum(step_ms)
     sweeps = sum(s["sweeps"] for s in stats)
     sweep_ms = sum(s["sweep_ms"] for s in stats)
-    if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * sweeps * pts / (total_ms / 1e3) / 1e9
+    from paper_1511_04292_gb300 import replicas
+    value, total_ms, _ = replicas.throughput(total_ms, float(sweeps * pts), device="cuda")
     ms_per_step = total_ms / args.steps
 
     # dominant kernel: the FP32 sweep; one launch applies T steps to every point
