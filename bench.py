@@ -58,6 +58,7 @@ def parse():
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
     ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
+    ap.add_argument("--variant", type=int, default=None, help="kernel-case f32: blocked sweep variant (0 or 1)")
     return ap.parse_args()
 
 
@@ -70,6 +71,8 @@ def run_kernel_case(args):
     plan = srj.Plan((n, n), 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
     if args.T is not None:
         plan.set_temporal_depth(args.T)
+    if args.variant is not None:
+        plan.set_sweep_variant(args.variant)
     f = torch.from_numpy(W.random_field((n, n), 1)).cuda()
     u = torch.from_numpy(W.random_field((n, n), 2)).cuda()
     plan.steps(f, u, 0, args.count)
@@ -262,6 +265,7 @@ def run_srj(args):
     u = torch.empty_like(u0)
     plan = srj.Plan.from_table(dims, args.P, "mixed")
     tuned_T, tuned_us = plan.autotune()
+    tuned_variant = plan.sweep_variant()
     M = plan.info()["M"]
     launches_per_cycle = -(-M // tuned_T)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
@@ -304,7 +308,7 @@ def run_srj(args):
     launches = sum(s["cycles"] for s in stats) * launches_per_cycle
     launch_avg_ms = sweep_ms / launches
     achieved = 12.0 * pts / (launch_avg_ms / 1e3) / 1e9
-    kname = "k_sweep_f32<2>" if tuned_T == 1 else "k_sweep_f32_tb<%d>" % tuned_T
+    kname = "k_sweep_f32<2>" if tuned_T == 1 else ("k_sweep_f32_tbp<%d>" if tuned_variant else "k_sweep_f32_tb<%d>") % tuned_T
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": 12 * pts,
@@ -368,7 +372,7 @@ def run_srj(args):
     line = {"metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
-            "time_to_tol_s": ms_per_step / 1e3, "temporal_depth": tuned_T, "autotune_us_per_step": tuned_us, "cycles": stats[-1]["cycles"], "sweeps_per_solve": stats[-1]["sweeps"],
+            "time_to_tol_s": ms_per_step / 1e3, "temporal_depth": tuned_T, "sweep_variant": tuned_variant, "autotune_us_per_step": tuned_us, "cycles": stats[-1]["cycles"], "sweeps_per_solve": stats[-1]["sweeps"],
             "final_rel_residual": stats[-1]["rel_res"],
             "fp64_comparator": fp64, "speedup_vs_fp64_time_to_tol": fp64["time_to_tol_s"] / (ms_per_step / 1e3),
             "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,

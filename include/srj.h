@@ -130,13 +130,24 @@ int srj_plan_info(srj_plan_t plan, int64_t *M, double *kappa_min, double *log10_
  */
 int srj_plan_set_temporal_depth(srj_plan_t plan, int T);
 
+/*
+ * srj_plan_set_sweep_variant -- blocked FP32 sweep strategy of a 2-D mixed plan:
+ * 0 = one thread block per tile; 1 = persistent blocks (2 per SM) that walk the
+ * tiles and prefetch the next tile with cp.async while computing the current
+ * one.  Both give the same bits.  Re-captures the cycle graph.
+ */
+int srj_plan_set_sweep_variant(srj_plan_t plan, int variant);
+
+/* srj_plan_sweep_variant -- current sweep variant (host output). */
+int srj_plan_sweep_variant(srj_plan_t plan, int *variant);
+
 /* srj_plan_temporal_depth -- current temporal depth (host output). */
 int srj_plan_temporal_depth(srj_plan_t plan, int *T);
 
 /*
  * srj_plan_autotune -- time the plan's sweep for every admissible temporal depth
- * on its own workspaces (a few hundred steps each, CUDA events on `stream`),
- * keep the fastest and report it (best_T, microseconds per step; either output
+ * and sweep variant on its own workspaces (a few hundred steps each, CUDA
+ * events on `stream`), keep the fastest and report it (best_T, microseconds per step; either output
  * may be NULL).  The workspaces' contents are overwritten; srj_solve resets
  * them.  Blocks until done.
  */

@@ -107,6 +107,15 @@ class Plan:
         check(self._lib.srj_plan_temporal_depth(self._h, ctypes.byref(T)))
         return T.value
 
+    def set_sweep_variant(self, v):
+        """0: one block per tile; 1: persistent blocks with cp.async prefetch (2-D mixed plans)."""
+        check(self._lib.srj_plan_set_sweep_variant(self._h, int(v)))
+
+    def sweep_variant(self):
+        v = ctypes.c_int()
+        check(self._lib.srj_plan_sweep_variant(self._h, ctypes.byref(v)))
+        return v.value
+
     def autotune(self, stream=None):
         """Pick the fastest temporal depth on this plan's grid; returns (T, us per step)."""
         T = ctypes.c_int(); us = ctypes.c_float()

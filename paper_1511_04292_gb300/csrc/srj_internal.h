@@ -80,6 +80,10 @@ cudaError_t tb_prepare();  // kernel attributes (dynamic shared memory)
 // rin (pitched float32), writes the interior of eout (eout != ein).
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
                                 const TbSteps& steps, cudaStream_t s);
+// Persistent variant: `blocks` blocks walk the tiles, prefetching the next one
+// with cp.async while computing the current one.  Same results bit for bit.
+cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,
+                                 const TbSteps& steps, int blocks, cudaStream_t s);
 
 // ---- batched solver (independent 2-D problems, mixed precision) -----------
 

@@ -235,6 +235,8 @@ struct srj_plan {
 
     // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
     int tdepth = 1;
+    int variant = 0;     // blocked sweep: 0 = one block per tile, 1 = persistent with cp.async prefetch
+    int sm_count = 152;
     float* e_final = nullptr;  // buffer holding the correction after one cycle
     int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
     int* host_err = nullptr;   // pinned copy
@@ -275,7 +277,8 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
             srj::TbSteps st{};
             st.T = n;
             for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
-            err = srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, s);
+            err = p->variant == 1 ? srj::launch_sweep_f32_tbp(p->g, in, p->r32, out, st, 2 * p->sm_count, s)
+                                  : srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, s);
         }
         std::swap(in, out);
         k += n;
@@ -491,6 +494,9 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
             return bail(fail(SRJ_ERR_CUDA, "set-up of the blocked sweep failed"));
         }
         p->tdepth = 4;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) == cudaSuccess && sms > 0)
+            p->sm_count = sms;
     }
     int rc = recapture(p);
     if (rc != SRJ_OK) return bail(rc);
@@ -516,6 +522,20 @@ int srj_plan_set_temporal_depth(srj_plan_t plan, int T) {
     return set_depth(plan, T);
 }
 
+int srj_plan_set_sweep_variant(srj_plan_t plan, int v) {
+    int rc = check_plan(plan);
+    if (rc) return rc;
+    if (v != 0 && v != 1) return fail(SRJ_ERR_INVALID_ARG, "sweep variant must be 0 or 1");
+    plan->variant = v;
+    return recapture(plan);
+}
+
+int srj_plan_sweep_variant(srj_plan_t plan, int* v) {
+    if (!plan || !v) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    *v = plan->variant;
+    return SRJ_OK;
+}
+
 int srj_plan_temporal_depth(srj_plan_t plan, int* T) {
     if (!plan || !T) return fail(SRJ_ERR_INVALID_ARG, "NULL argument");
     *T = plan->tdepth;
@@ -526,13 +546,17 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     int rc = check_plan(p);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    int cands[8] = {1, 2, 3, 4, 5, 6, 7, 8};
-    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 8 : 1;
+    // candidates (T, variant): the unblocked sweep, then both blocked variants for T = 2..8
+    int candT[15] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
+    int candV[15] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1};
+    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 15 : 1;
+    int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;
     int bestT = p->tdepth;
     for (int ci = 0; ci < ncand; ++ci) {
-        p->tdepth = cands[ci];
+        p->tdepth = candT[ci];
+        p->variant = candV[ci];
         float* fin = nullptr;
         float ms_best = INFINITY;
         for (int rep = 0; rep < 3; ++rep) {
@@ -552,8 +576,9 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
             SRJ_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
             ms_best = std::min(ms_best, ms);
         }
-        if (ms_best < best) { best = ms_best; bestT = cands[ci]; }
+        if (ms_best < best) { best = ms_best; bestT = candT[ci]; bestV = candV[ci]; }
     }
+    p->variant = bestV;
     SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     if (*p->host_err) { cudaMemset(p->d_err, 0, sizeof(int)); return fail(SRJ_ERR_TIMEOUT, "bounded wait gave up"); }

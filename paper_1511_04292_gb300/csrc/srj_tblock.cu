@@ -158,6 +158,102 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
                   false, xch);
 }
 
+__device__ inline void cp_async16(void* smem_dst, const void* gsrc, unsigned src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Persistent form: gridDim.x blocks walk the tiles (x fastest); while a block
+// computes one tile, the band rows of its next tile are copied by cp.async into
+// a shared staging area.  Each lane stages exactly the float4s it reads back,
+// so the staging needs no barrier, only the lane's own cp.async wait.
+template <int T>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_sweep_f32_tbp(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
+                TbSteps steps, int tiles_x, int ntiles) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int TX = kSX - 2 * HX;
+    constexpr int TY = kSY - 2 * T;
+    __shared__ float4 xch[2 * 2 * kWarps * 32];
+    extern __shared__ float4 stage[];  // [2][kSY][32]: e rows, then r rows
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
+    float4* se = stage;
+    float4* sr = stage + kSY * 32;
+
+    auto prefetch = [&](int tile) {
+        const int bx = tile % tiles_x, by = tile / tiles_x;
+        const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
+        const int col = X0 + 3 + 4 * lane;  // multiple of 4: each float4 wholly in or out of the buffer
+        const bool colok = col >= 0 && col + 4 <= g.p32;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            const int64_t y = (int64_t)Y0 + row;
+            const bool ok = colok && y >= 0 && y < rows;
+            const int64_t off = ok ? y * g.p32 + col : 0;
+            cp_async16(&se[row * 32 + lane], ein + off, ok ? 16u : 0u);
+            cp_async16(&sr[row * 32 + lane], rin + off, ok ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+
+    int tile = blockIdx.x;
+    if (tile < ntiles) prefetch(tile);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int bx = tile % tiles_x, by = tile / tiles_x;
+        const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
+        cp_async_wait_all();
+        float4 e[kBand], rr[kBand];
+        bool iny[kBand];
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            e[i] = se[row * 32 + lane];
+            rr[i] = sr[row * 32 + lane];
+            const int y = Y0 + row;
+            iny[i] = y >= 1 && y <= g.ny;
+        }
+        if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
+        bool inx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = X0 + 4 * lane + j;
+            inx[j] = x >= 1 && x <= g.nx;
+        }
+        const bool interior = X0 >= 1 && X0 + kSX - 1 <= g.nx && Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
+        if (interior) band_steps<T, false>(e, rr, xch, steps.c, steps.T, lane, w, inx, iny);
+        else          band_steps<T, true>(e, rr, xch, steps.c, steps.T, lane, w, inx, iny);
+        const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+        if (lane >= lane_lo && lane < lane_hi) {
+#pragma unroll
+            for (int i = 0; i < kBand; ++i) {
+                const int row = w * kBand + i;
+                if (row < T || row >= T + TY) continue;
+                const int y = Y0 + row;
+                if (y < 1 || y > g.ny) continue;
+                const int x = X0 + 4 * lane;
+                float* dst = eout + (int64_t)y * g.p32 + x + 3;
+                if (inx[0] && inx[3]) {
+                    *reinterpret_cast<float4*>(dst) = e[i];
+                } else {
+                    if (inx[0]) dst[0] = e[i].x;
+                    if (inx[1]) dst[1] = e[i].y;
+                    if (inx[2]) dst[2] = e[i].z;
+                    if (inx[3]) dst[3] = e[i].w;
+                }
+            }
+        }
+        // the next tile's first exchange must not overwrite a slot a slower
+        // warp is still reading in this tile's last step
+        __syncthreads();
+    }
+    cp_async_wait_all();
+}
+
 // Batched form: one launch covers the tiles of every problem of a batch; each
 // block finds its problem in the tile table and advances it by
 // n = min(T, M - k) steps of its own cycle order.  Problems that have finished
@@ -187,9 +283,17 @@ size_t smem_bytes() { return 0; }
 
 int tb_max_steps() { return 8; }
 
+constexpr size_t kStageBytes = 2 * kSY * 32 * sizeof(float4);  // 64 KB
+
 template <int T>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_sweep_f32_tb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes());
+    return cudaFuncSetAttribute(k_sweep_f32_tbp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+}
+
+template <int T>
+void launch_P(unsigned grid, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
+              const TbSteps& st, int tiles_x, int ntiles) {
+    k_sweep_f32_tbp<T><<<grid, kWarps * 32, kStageBytes, s>>>(ein, rin, eout, g, st, tiles_x, ntiles);
 }
 
 template <int T>
@@ -232,6 +336,27 @@ cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* ri
         case 6: launch_T<6>(grd, s, me, mr, eout, g, steps); break;
         case 7: launch_T<7>(grd, s, me, mr, eout, g, steps); break;
         default: launch_T<8>(grd, s, me, mr, eout, g, steps); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,
+                                 const TbSteps& steps, int blocks, cudaStream_t s) {
+    if (g.nd != 2 || steps.T < 1 || steps.T > 8 || blocks < 1) return cudaErrorInvalidValue;
+    const int HX = steps.T <= 4 ? 4 : 8;
+    const int TX = kSX - 2 * HX, TY = kSY - 2 * steps.T;
+    const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
+    const int ntiles = tx * ty;
+    const unsigned grid = (unsigned)std::min(blocks, ntiles);
+    switch (steps.T) {
+        case 1: launch_P<1>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 2: launch_P<2>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 3: launch_P<3>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 4: launch_P<4>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 5: launch_P<5>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 6: launch_P<6>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        case 7: launch_P<7>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
+        default: launch_P<8>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
     }
     return cudaGetLastError();
 }

@@ -258,14 +258,17 @@ def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
     plan = srj.Plan(dims, h, omega, q, order, "mixed")
     fd = dev(f)
     for count, first in [(len(order), 0), (13, 5)]:
+        plan.set_sweep_variant(0)
         plan.set_temporal_depth(1)
         ref = dev(u)
         plan.steps(fd, ref, first, count)
-        for T in range(2, 9):
-            plan.set_temporal_depth(T)
-            got = dev(u)
-            plan.steps(fd, got, first, count)
-            assert torch.equal(got, ref), (dims, T, count, first)
+        for variant in (0, 1):
+            plan.set_sweep_variant(variant)
+            for T in range(2, 9):
+                plan.set_temporal_depth(T)
+                got = dev(u)
+                plan.steps(fd, got, first, count)
+                assert torch.equal(got, ref), (dims, variant, T, count, first)
 
 
 def test_autotune_picks_a_valid_depth_and_solve_still_converges():
