@@ -62,11 +62,24 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
             float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
             if (lane == 0) lf = 0.f;
             if (lane == 31) rt = 0.f;
-            float4 o;
-            o.x = upd(c, two_d, cur.x, ((lf + cur.y) + up.x) + dn.x, rr[i].x);
-            o.y = upd(c, two_d, cur.y, ((cur.x + cur.z) + up.y) + dn.y, rr[i].y);
-            o.z = upd(c, two_d, cur.z, ((cur.y + cur.w) + up.z) + dn.z, rr[i].z);
-            o.w = upd(c, two_d, cur.w, ((cur.z + rt) + up.w) + dn.w, rr[i].w);
+            // Packed FP32x2 form of the single-step update: per component the
+            // same operations in the same order as upd() with
+            // nb = ((left + right) + up) + down (x,y pair and z,w pair).
+            const float2 m4 = make_float2(-two_d, -two_d);
+            const float2 cv = make_float2(c, c);
+            const float2 mid = make_float2(cur.y, cur.z);
+            float2 s0 = __fadd2_rn(make_float2(lf, cur.x), mid);    // (lf + y, x + z)
+            float2 s1 = __fadd2_rn(mid, make_float2(cur.w, rt));    // (y + w, z + rt)
+            s0 = __fadd2_rn(s0, make_float2(up.x, up.y));
+            s1 = __fadd2_rn(s1, make_float2(up.z, up.w));
+            s0 = __fadd2_rn(s0, make_float2(dn.x, dn.y));
+            s1 = __fadd2_rn(s1, make_float2(dn.z, dn.w));
+            s0 = __fadd2_rn(s0, make_float2(rr[i].x, rr[i].y));
+            s1 = __fadd2_rn(s1, make_float2(rr[i].z, rr[i].w));
+            const float2 c0 = make_float2(cur.x, cur.y), c1 = make_float2(cur.z, cur.w);
+            const float2 o0 = __ffma2_rn(cv, __ffma2_rn(m4, c0, s0), c0);
+            const float2 o1 = __ffma2_rn(cv, __ffma2_rn(m4, c1, s1), c1);
+            float4 o = make_float4(o0.x, o0.y, o1.x, o1.y);
             if (MASKED) {
                 o.x = (iny[i] && inx[0]) ? o.x : cur.x;
                 o.y = (iny[i] && inx[1]) ? o.y : cur.y;
