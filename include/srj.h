@@ -132,9 +132,10 @@ int srj_plan_set_temporal_depth(srj_plan_t plan, int T);
 
 /*
  * srj_plan_set_sweep_variant -- blocked FP32 sweep strategy of a 2-D mixed plan:
- * 0 = one thread block per tile; 1 = persistent blocks (2 per SM) that walk the
- * tiles and prefetch the next tile with cp.async while computing the current
- * one.  Both give the same bits.  Re-captures the cycle graph.
+ * 0 = one thread block of 8 warps per 128 x 64 tile; 1 = persistent blocks (2 per
+ * SM) that walk the tiles and prefetch the next tile with cp.async while
+ * computing the current one; 2 = one block of 16 warps per 128 x 128 tile (less
+ * halo recomputation).  All give the same bits.  Re-captures the cycle graph.
  */
 int srj_plan_set_sweep_variant(srj_plan_t plan, int variant);
 

@@ -78,8 +78,9 @@ int tb_max_steps();
 cudaError_t tb_prepare();  // kernel attributes (dynamic shared memory)
 // T = steps.T consecutive FP32 steps in one launch: reads ein and the defect
 // rin (pitched float32), writes the interior of eout (eout != ein).
+// warps: 8 (128 x 64 tiles) or 16 (128 x 128 tiles).
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
-                                const TbSteps& steps, cudaStream_t s);
+                                const TbSteps& steps, int warps, cudaStream_t s);
 // Persistent variant: `blocks` blocks walk the tiles, prefetching the next one
 // with cp.async while computing the current one.  Same results bit for bit.
 cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,

@@ -278,7 +278,7 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
             st.T = n;
             for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
             err = p->variant == 1 ? srj::launch_sweep_f32_tbp(p->g, in, p->r32, out, st, 2 * p->sm_count, s)
-                                  : srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, s);
+                                  : srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, p->variant == 2 ? 16 : 8, s);
         }
         std::swap(in, out);
         k += n;
@@ -525,7 +525,7 @@ int srj_plan_set_temporal_depth(srj_plan_t plan, int T) {
 int srj_plan_set_sweep_variant(srj_plan_t plan, int v) {
     int rc = check_plan(plan);
     if (rc) return rc;
-    if (v != 0 && v != 1) return fail(SRJ_ERR_INVALID_ARG, "sweep variant must be 0 or 1");
+    if (v < 0 || v > 2) return fail(SRJ_ERR_INVALID_ARG, "sweep variant must be 0, 1 or 2");
     plan->variant = v;
     return recapture(plan);
 }
@@ -547,9 +547,9 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     // candidates (T, variant): the unblocked sweep, then both blocked variants for T = 2..8
-    int candT[15] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
-    int candV[15] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1};
-    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 15 : 1;
+    int candT[22] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
+    int candV[22] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2};
+    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 22 : 1;
     int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;

@@ -37,7 +37,7 @@ __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) 
 // (float4, 4 consecutive columns per lane) and the defect rr[i].  Only the
 // band's top and bottom rows cross warps, through a double-buffered shared
 // slot, so each step costs one barrier and four shared-memory accesses per lane.
-template <int T, bool MASKED>
+template <int T, bool MASKED, int W = kWarps>
 __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr)[kBand], float4* xch,
                                            const float (&cs)[8], int n, int lane, int w, const bool (&inx)[4],
                                            const bool (&iny)[kBand]) {
@@ -47,21 +47,21 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
     for (int t = 0; t < T; ++t) {
         if (t >= n) break;  // n is uniform over the block
         const float c = cs[t];
-        float4* slot = xch + (t & 1) * (2 * kWarps * 32);
+        float4* slot = xch + (t & 1) * (2 * W * 32);
         slot[(2 * w) * 32 + lane] = e[0];              // top row of this band
         slot[(2 * w + 1) * 32 + lane] = e[kBand - 1];  // bottom row
         __syncthreads();
         const float4 above = (w > 0) ? slot[(2 * (w - 1) + 1) * 32 + lane] : zero;
-        const float4 below = (w + 1 < kWarps) ? slot[(2 * (w + 1)) * 32 + lane] : zero;
+        const float4 below = (w + 1 < W) ? slot[(2 * (w + 1)) * 32 + lane] : zero;
         float4 up = above;  // old value of the row above the one being updated
 #pragma unroll
         for (int i = 0; i < kBand; ++i) {
             const float4 cur = e[i];
             const float4 dn = (i + 1 < kBand) ? e[i + 1] : below;
-            float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
-            float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            if (lane == 0) lf = 0.f;
-            if (lane == 31) rt = 0.f;
+            // lanes 0 and 31 receive their own values: those columns lie in the
+            // stale halo of the tile, so what they compute is never stored
+            const float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            const float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
             // Packed FP32x2 form of the single-step update: per component the
             // same operations in the same order as upd() with
             // nb = ((left + right) + up) + down (x,y pair and z,w pair).
@@ -96,13 +96,14 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
 // X0 / Y0: padded coordinates of the tile's first column / row.  fresh: the
 // input iterate is identically zero (start of a defect-correction cycle), so it
 // is not read.
-template <int T>
+template <int T, int W = kWarps>
 __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const float* __restrict__ rin,
                                            float* __restrict__ eout, int nx, int ny, int64_t p32, int64_t rows,
                                            const float (&cs)[8], int n, int bx, int by, bool fresh, float4* xch) {
     constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int SY = W * kBand;  // tile rows
     constexpr int TX = kSX - 2 * HX;
-    constexpr int TY = kSY - 2 * T;
+    constexpr int TY = SY - 2 * T;
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int X0 = 1 + TX * bx - HX;
@@ -135,9 +136,9 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
         inx[j] = x >= 1 && x <= nx;
     }
     // tiles whose every point is an interior grid point need no masking
-    const bool interior = X0 >= 1 && X0 + kSX - 1 <= nx && Y0 >= 1 && Y0 + kSY - 1 <= ny;
-    if (interior) band_steps<T, false>(e, rr, xch, cs, n, lane, w, inx, iny);
-    else          band_steps<T, true>(e, rr, xch, cs, n, lane, w, inx, iny);
+    const bool interior = X0 >= 1 && X0 + kSX - 1 <= nx && Y0 >= 1 && Y0 + SY - 1 <= ny;
+    if (interior) band_steps<T, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
+    else          band_steps<T, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
 
     // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
@@ -161,14 +162,14 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+template <int T, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
 k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
                TbSteps steps) {
-    __shared__ float4 xch[2 * 2 * kWarps * 32];  // [slot][warp][top/bottom][lane]
+    __shared__ float4 xch[2 * 2 * W * 32];  // [slot][warp][top/bottom][lane]
     const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
-    tile_sweep<T>(ein, rin, eout, g.nx, g.ny, g.p32, rows, steps.c, steps.T, (int)blockIdx.x, (int)blockIdx.y,
-                  false, xch);
+    tile_sweep<T, W>(ein, rin, eout, g.nx, g.ny, g.p32, rows, steps.c, steps.T, (int)blockIdx.x, (int)blockIdx.y,
+                     false, xch);
 }
 
 __device__ inline void cp_async16(void* smem_dst, const void* gsrc, unsigned src_bytes) {
@@ -309,10 +310,25 @@ void launch_P(unsigned grid, cudaStream_t s, const float* ein, const float* rin,
     k_sweep_f32_tbp<T><<<grid, kWarps * 32, kStageBytes, s>>>(ein, rin, eout, g, st, tiles_x, ntiles);
 }
 
-template <int T>
+template <int T, int W>
 void launch_T(dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
               const TbSteps& st) {
-    k_sweep_f32_tb<T><<<grd, kWarps * 32, smem_bytes(), s>>>(ein, rin, eout, g, st);
+    k_sweep_f32_tb<T, W><<<grd, W * 32, smem_bytes(), s>>>(ein, rin, eout, g, st);
+}
+
+template <int W>
+void launch_W(int T, dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
+              const TbSteps& st) {
+    switch (T) {
+        case 1: launch_T<1, W>(grd, s, ein, rin, eout, g, st); break;
+        case 2: launch_T<2, W>(grd, s, ein, rin, eout, g, st); break;
+        case 3: launch_T<3, W>(grd, s, ein, rin, eout, g, st); break;
+        case 4: launch_T<4, W>(grd, s, ein, rin, eout, g, st); break;
+        case 5: launch_T<5, W>(grd, s, ein, rin, eout, g, st); break;
+        case 6: launch_T<6, W>(grd, s, ein, rin, eout, g, st); break;
+        case 7: launch_T<7, W>(grd, s, ein, rin, eout, g, st); break;
+        default: launch_T<8, W>(grd, s, ein, rin, eout, g, st); break;
+    }
 }
 
 template <int T>
@@ -333,23 +349,13 @@ cudaError_t tb_prepare() {
 }
 
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
-                                const TbSteps& steps, cudaStream_t s) {
-    if (g.nd != 2 || steps.T < 1 || steps.T > 8) return cudaErrorInvalidValue;
-    const float* me = ein;
-    const float* mr = rin;
+                                const TbSteps& steps, int warps, cudaStream_t s) {
+    if (g.nd != 2 || steps.T < 1 || steps.T > 8 || (warps != 8 && warps != 16)) return cudaErrorInvalidValue;
     const int HX = steps.T <= 4 ? 4 : 8;
-    const int TX = kSX - 2 * HX, TY = kSY - 2 * steps.T;
+    const int TX = kSX - 2 * HX, TY = warps * kBand - 2 * steps.T;
     dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
-    switch (steps.T) {
-        case 1: launch_T<1>(grd, s, me, mr, eout, g, steps); break;
-        case 2: launch_T<2>(grd, s, me, mr, eout, g, steps); break;
-        case 3: launch_T<3>(grd, s, me, mr, eout, g, steps); break;
-        case 4: launch_T<4>(grd, s, me, mr, eout, g, steps); break;
-        case 5: launch_T<5>(grd, s, me, mr, eout, g, steps); break;
-        case 6: launch_T<6>(grd, s, me, mr, eout, g, steps); break;
-        case 7: launch_T<7>(grd, s, me, mr, eout, g, steps); break;
-        default: launch_T<8>(grd, s, me, mr, eout, g, steps); break;
-    }
+    if (warps == 16) launch_W<16>(steps.T, grd, s, ein, rin, eout, g, steps);
+    else             launch_W<8>(steps.T, grd, s, ein, rin, eout, g, steps);
     return cudaGetLastError();
 }
 

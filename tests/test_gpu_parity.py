@@ -262,7 +262,7 @@ def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
         plan.set_temporal_depth(1)
         ref = dev(u)
         plan.steps(fd, ref, first, count)
-        for variant in (0, 1):
+        for variant in (0, 1, 2):
             plan.set_sweep_variant(variant)
             for T in range(2, 9):
                 plan.set_temporal_depth(T)
