@@ -37,6 +37,10 @@ P = 10
 TOL = 1e-10
 SEED_F = 2
 MAX_CYCLES = 200
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel at
+# this grid size (warm cache, --cache-control none), keyed by (kernel, n).
+# Entries are removed when the kernel changes.
+MEASURED_TRAFFIC = {("k_sweep_f32_tb<8,8>", 4096): 202_964_480}
 
 
 def parse():
@@ -264,7 +268,12 @@ def run_srj(args):
     u0 = torch.from_numpy(u0_h).cuda()
     u = torch.empty_like(u0)
     plan = srj.Plan.from_table(dims, args.P, "mixed")
-    tuned_T, tuned_us = plan.autotune()
+    if args.T is not None:
+        plan.set_temporal_depth(args.T)
+        plan.set_sweep_variant(args.variant or 0)
+        tuned_T, tuned_us = args.T, float("nan")
+    else:
+        tuned_T, tuned_us = plan.autotune()
     tuned_variant = plan.sweep_variant()
     M = plan.info()["M"]
     launches_per_cycle = -(-M // tuned_T)
@@ -308,9 +317,14 @@ def run_srj(args):
     launches = sum(s["cycles"] for s in stats) * launches_per_cycle
     launch_avg_ms = sweep_ms / launches
     achieved = 12.0 * pts / (launch_avg_ms / 1e3) / 1e9
-    kname = "k_sweep_f32<2>" if tuned_T == 1 else ("k_sweep_f32_tbp<%d>" if tuned_variant else "k_sweep_f32_tb<%d>") % tuned_T
+    if tuned_T == 1:
+        kname = "k_sweep_f32<2>"
+    elif tuned_variant == 1:
+        kname = "k_sweep_f32_tbp<%d>" % tuned_T
+    else:
+        kname = "k_sweep_f32_tb<%d,%d>" % (tuned_T, 16 if tuned_variant == 2 else 8)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get((kname, n)),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": 12 * pts,
                 "avg_launch_us": launch_avg_ms * 1e3, "steps_per_launch": tuned_T,
                 "effective_gbs_per_step": 12.0 * pts * sweeps / (sweep_ms / 1e3) / 1e9}
