@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--impl", default="srj", choices=["srj", "reference"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--P", type=int, default=P)
-    ap.add_argument("--fp64-cycles", type=int, default=1,
+    ap.add_argument("--fp64-cycles", type=int, default=0,
                     help="cycles of the plain FP64 comparator to time (0 = run it to tolerance)")
     ap.add_argument("--cpu-sweeps", type=int, default=4, help="oracle sweeps in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

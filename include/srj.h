@@ -281,6 +281,27 @@ const char *srj_batch_last_error(void);
 int srj_gradient(srj_plan_t plan, const double *grad_u, double *lambda, double *grad_f, double *grad_g, double tol,
                  int64_t max_cycles, void *stream, srj_stats_t *stats);
 
+/*
+ * srj_schedule_optimal -- host-only optimal SRJ parameters (Sect. 3): for P levels
+ * (1..32) and the spectral bound kappa_min in (0, 1), the weights omega[P]
+ * (decreasing), fractions beta[P] (sum 1) and, if kappa_int is not NULL, the P-1
+ * interior maxima of Gamma, minimising max over [kappa_min, 2] of
+ * Gamma(kappa) = prod_i |1 - omega_i kappa|^beta_i (Eq. Gamma).  The reduced system
+ * S(omega, kappa) of Sect. 3.5 (beta from Theorem 2, equal maxima, optimality in
+ * Lagrange-multiplier form) is solved by Levenberg-Marquardt, level by level with the
+ * initial guesses of Sect. 3.3.  Returns SRJ_ERR_BAD_SCHEDULE if no solution is
+ * found (large P at small resolution, as the paper reports).  Needs no GPU.
+ */
+int srj_schedule_optimal(int P, double kappa_min, double *omega, double *beta, double *kappa_int);
+
+/*
+ * srj_schedule_for_grid -- host-only: optimal weights at the grid's kappa_min and
+ * integer repetitions q_i = floor(beta_i / beta_1) (Sect. 4.3); checks that the
+ * integer scheme contracts on the grid (SRJ_ERR_BAD_SCHEDULE otherwise).  Outputs
+ * omega[P], q[P] and M = sum q (M_out may be NULL).  Needs no GPU.
+ */
+int srj_schedule_for_grid(int ndim, const int64_t *dims, int P, double *omega, int32_t *q, int64_t *M_out);
+
 /* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 

@@ -82,6 +82,13 @@ class Plan:
         row = schedules.lookup(len(dims), n, int(P))
         return cls(dims, 1.0 / (n + 1) if h is None else h, row["omega"], row["q"], row["order"], precision)
 
+    @classmethod
+    def auto(cls, dims, P, precision="fp64", h=None):
+        """Plan with the optimal P-level schedule for this grid from the library's
+        native planner (Sect. 3, floor rule of Sect. 4.3) and its own cycle order."""
+        omega, q = schedules.for_grid(dims, P)
+        return cls(dims, 1.0 / (max(int(v) for v in dims) + 1) if h is None else h, omega, q, None, precision)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.srj_plan_destroy(self._h)

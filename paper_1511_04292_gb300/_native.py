@@ -16,7 +16,7 @@ _ROOT = _PKG.parent
 _CSRC = _PKG / "csrc"
 _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
-SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_batch.cu", "srj_noalloc.cu"]
+SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -115,6 +115,8 @@ SIGNATURES = {
     "srj_kappa_min": (_I, [_I, _I64P, _DP]),
     "srj_schedule_check": (_I, [_I, _DP, _I32P, _D, _D, _DP]),
     "srj_schedule_order": (_I, [_I, _DP, _I32P, _D, _I32P]),
+    "srj_schedule_optimal": (_I, [_I, _D, _DP, _DP, _DP]),
+    "srj_schedule_for_grid": (_I, [_I, _I64P, _I, _DP, _I32P, _I64P]),
     "srj_steps_f32_noalloc": (_I, [_I, _I64P, _D, _I64, _DP, _VP, _VP, _VP]),
     "srj_noalloc_last_error": (ctypes.c_char_p, []),
     "srj_batch_create": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(BatchProblem), _I]),

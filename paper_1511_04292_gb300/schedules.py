@@ -41,3 +41,25 @@ def lookup(ndim, n, P):
             out["order"] = decode_order(r["order"])
             return out
     raise KeyError("no schedule for ndim=%d n=%d P=%d (have %s)" % (ndim, n, P, available()))
+
+
+def optimal(P, kappa_min):
+    """Optimal (omega, beta, kappa_int) from the library's native planner (Sect. 3)."""
+    import ctypes
+    from ._native import check, lib
+    om = np.empty(P); be = np.empty(P); ki = np.empty(max(P - 1, 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib().srj_schedule_optimal(int(P), float(kappa_min), om.ctypes.data_as(dp), be.ctypes.data_as(dp),
+                                     ki.ctypes.data_as(dp)))
+    return om, be, ki[:P - 1]
+
+
+def for_grid(dims, P):
+    """(omega, q) for a Dirichlet grid from the native planner (Sect. 3 + Sect. 4.3)."""
+    import ctypes
+    from ._native import check, lib
+    om = np.empty(P); q = np.empty(P, dtype=np.int32); M = ctypes.c_int64()
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    check(lib().srj_schedule_for_grid(len(dims), d, int(P), om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(M)))
+    return om, q

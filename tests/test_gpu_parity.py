@@ -297,3 +297,18 @@ def test_temporal_depth_rules():
     assert p2.temporal_depth() == 4
     with pytest.raises(srj.SRJError):
         p2.set_temporal_depth(9)
+
+
+def test_auto_plan_from_native_planner_converges():
+    """A plan built entirely by the library (native planner + its own cycle order)
+    on a ragged grid solves to tolerance (mixed and FP64)."""
+    dims = (300, 211)
+    f = W.random_field(dims, 71)
+    u0 = W.random_field(dims, 72); u0[1:-1, 1:-1] = 0
+    for prec in ("mixed", "fp64"):
+        plan = srj.Plan.auto(dims, 8, prec)
+        ud = dev(u0)
+        plan.solve(dev(f), ud, 1e-10, 500)
+        r0, _ = oracle.residual(dims, plan.h, f, u0)
+        l2, _ = oracle.residual(dims, plan.h, f, ud.cpu().numpy())
+        assert l2 <= 1e-10 * r0 * (1 + 1e-9)
