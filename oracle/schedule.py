@@ -316,9 +316,10 @@ def _order_drift_once(omega, q, kappa_m, kappa_max, samples):
 
 
 DRIFT_GRIDS = (1000, 2000, 3000, 4000)
+TAIL_STEPS = 4
 
 
-def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, grids=DRIFT_GRIDS):
+def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, grids=DRIFT_GRIDS, tail=TAIL_STEPS):
     """Order of the M weight applications inside one cycle.
 
     Sect. 5.1 notes that the largest over-relaxations must be spread over the
@@ -332,15 +333,27 @@ def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, grids=DRIFT_GRIDS):
     grid leaves a cluster of large weights late in the cycle), so the pass is
     run on geometric grids of each size in `grids` and the order with the
     smallest worst-window growth (then suffix growth) on a 4001-point grid is
-    kept.  Returns level indices (0-based) of length M.
+    kept.  The last min(tail, q_P) steps of the cycle use the smallest weight
+    omega_P: rounding errors made late in the cycle are amplified most at
+    kappa ~ 2, which omega_P damps by |1 - 2 omega_P| per step; the greedy
+    orders the other steps.  Returns level indices (0-based) of length M.
     """
+    q = [int(v) for v in q]
+    P = len(q)
+    k = min(int(tail), q[-1]) if P > 1 else 0
+    body_q = list(q)
+    body_q[-1] -= k
     best = None
-    for n in grids:
-        o = _order_drift_once(omega, q, kappa_m, kappa_max, n)
-        key = window_growth(omega, o, kappa_m, kappa_max, samples=4001)
-        if best is None or key < best[0]:
-            best = (key, o)
-    return best[1]
+    if sum(body_q) > 0:
+        for n in grids:
+            o = _order_drift_once(omega, body_q, kappa_m, kappa_max, n)
+            key = window_growth(omega, o, kappa_m, kappa_max, samples=4001)
+            if best is None or key < best[0]:
+                best = (key, o)
+        body = best[1]
+    else:
+        body = np.empty(0, dtype=np.int64)
+    return np.concatenate([body, np.full(k, P - 1, dtype=np.int64)])
 
 
 def window_growth(omega, order, kappa_m, kappa_max=KAPPA_MAX, samples=2000):

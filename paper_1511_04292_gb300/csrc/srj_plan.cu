@@ -187,17 +187,29 @@ void order_growth(const std::vector<double>& w, const std::vector<int32_t>& orde
 }
 
 // The greedy pass depends on its sampling grid; run it on a few grids and keep
-// the order with the smallest worst-window growth (then suffix growth).
+// the order with the smallest worst-window growth (then suffix growth).  The
+// cycle ends with min(4, q_P) steps of the smallest weight: rounding made late
+// in a cycle is amplified most near kappa = 2, which omega_P damps by
+// |1 - 2 omega_P| per step.  The greedy orders the other steps.
 std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin) {
-    const int grids[4] = {1000, 2000, 3000, 4000};
+    const int P = (int)w.size();
+    const int tail = P > 1 ? std::min(4, q[P - 1]) : 0;
+    std::vector<int32_t> body_q(q);
+    body_q[P - 1] -= tail;
     std::vector<int32_t> best;
-    double bw = INFINITY, bs = INFINITY;
-    for (int K : grids) {
-        std::vector<int32_t> o = drift_order_once(w, q, kmin, K);
-        double wg, sg;
-        order_growth(w, o, kmin, 4001, &wg, &sg);
-        if (wg < bw || (wg == bw && sg < bs)) { bw = wg; bs = sg; best.swap(o); }
+    int64_t body_M = 0;
+    for (int v : body_q) body_M += v;
+    if (body_M > 0) {
+        const int grids[4] = {1000, 2000, 3000, 4000};
+        double bw = INFINITY, bs = INFINITY;
+        for (int K : grids) {
+            std::vector<int32_t> o = drift_order_once(w, body_q, kmin, K);
+            double wg, sg;
+            order_growth(w, o, kmin, 4001, &wg, &sg);
+            if (wg < bw || (wg == bw && sg < bs)) { bw = wg; bs = sg; best.swap(o); }
+        }
     }
+    for (int t = 0; t < tail; ++t) best.push_back(P - 1);
     return best;
 }
 
