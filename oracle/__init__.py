@@ -70,6 +70,16 @@ def _load():
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.srj_oracle_solve.restype = ctypes.c_int
+        lib.srj_oracle_sweep_op.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            dp, dp, dp, dp]
+        lib.srj_oracle_sweep_op.restype = None
+        lib.srj_oracle_residual_op.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.srj_oracle_residual_op.restype = None
+        lib.srj_oracle_solve_op.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64,
+                                            dp, dp, dp, ctypes.c_double, ctypes.c_int64, i64p,
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.srj_oracle_solve_op.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -180,3 +190,52 @@ def solve(dims, h, seq, f, u, tol, max_cycles):
                               ctypes.byref(cyc), ctypes.byref(r0), ctypes.byref(rel), ctypes.byref(linf))
     return dict(status=st, cycles=cyc.value, sweeps=cyc.value * len(seq), r0=r0.value,
                 rel=rel.value, linf=linf.value)
+
+
+# ---------------------------------------------------------------------------
+# Masked / diagonally shifted operator (Sect. 5.3 test B setting)
+# ---------------------------------------------------------------------------
+
+def _mask_ptr(mask, dims):
+    if mask is None:
+        return None
+    if mask.dtype != np.uint8 or not mask.flags.c_contiguous or mask.shape != padded_shape(dims):
+        raise ValueError("mask must be a C-contiguous uint8 array of shape %s" % (padded_shape(dims),))
+    return mask.ctypes.data
+
+
+def sweep_op(dims, h, omega, sigma, mask, f, u):
+    """One step with A = (2d + sigma) I - neighbours on the active points of mask."""
+    lib = _load()
+    _check(f, dims, "f"); _check(u, dims, "u")
+    out = np.empty_like(u)
+    lib.srj_oracle_sweep_op(len(dims), _dims3(dims), float(h), float(omega), float(sigma), _mask_ptr(mask, dims),
+                            f.ctypes.data, u.ctypes.data, out.ctypes.data)
+    return out
+
+
+def residual_op(dims, h, sigma, mask, f, u, want_r=False):
+    lib = _load()
+    _check(f, dims, "f"); _check(u, dims, "u")
+    r = np.empty_like(u) if want_r else None
+    l2 = ctypes.c_double(); linf = ctypes.c_double()
+    lib.srj_oracle_residual_op(len(dims), _dims3(dims), float(h), float(sigma), _mask_ptr(mask, dims), f.ctypes.data,
+                               u.ctypes.data, r.ctypes.data if want_r else None, ctypes.byref(l2), ctypes.byref(linf))
+    return (l2.value, linf.value, r) if want_r else (l2.value, linf.value)
+
+
+def solve_op(dims, h, sigma, mask, seq, f, u, tol, max_cycles):
+    lib = _load()
+    _check(f, dims, "f"); _check(u, dims, "u")
+    seq = np.ascontiguousarray(seq, dtype=np.float64)
+    cyc = ctypes.c_int64(); r0 = ctypes.c_double(); rel = ctypes.c_double()
+    st = lib.srj_oracle_solve_op(len(dims), _dims3(dims), float(h), float(sigma), _mask_ptr(mask, dims), len(seq),
+                                 seq.ctypes.data, f.ctypes.data, u.ctypes.data, float(tol), int(max_cycles),
+                                 ctypes.byref(cyc), ctypes.byref(r0), ctypes.byref(rel))
+    return dict(status=st, cycles=cyc.value, r0=r0.value, rel=rel.value)
+
+
+def shifted_kappa(kappa, ndim, sigma):
+    """Eigenvalue of D^-1 A for the shifted operator, from the unshifted one:
+    A = (2d + sigma) I - N, N = 2d (1 - kappa) on a sine mode."""
+    return (2 * ndim * kappa + sigma) / (2 * ndim + sigma)
