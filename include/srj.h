@@ -154,6 +154,27 @@ int srj_plan_temporal_depth(srj_plan_t plan, int *T);
  */
 int srj_plan_autotune(srj_plan_t plan, void *stream, int *best_T, float *best_us_per_step);
 
+/*
+ * srj_plan_set_operator -- replace the plan's operator by
+ *   (A u)_p = (2d + sigma) u_p - sum_{neighbours} u_q     on the active points p,
+ * the setting of the paper's Grad-Shafranov test B (Sect. 5.3): the SRJ
+ * iteration runs only inside a region given by `mask` (device, uint8, padded
+ * layout; nonzero = active interior point, 0 = held at its value in u, which
+ * then acts as Dirichlet data; NULL = every interior point active), and Eq.
+ * GS_linear's linear term appears as a diagonal shift: sigma = -C^2 h^2 for
+ * Laplace(u) + C^2 u = rhs (written -Laplace(u) - C^2 u = f), sigma = +k^2 h^2
+ * for a screened Poisson operator.  sigma = 0 and mask = NULL restore the plain
+ * operator (same bits as before).  The weights are renormalised by the diagonal
+ * and the contraction check is redone on the shifted spectrum
+ * [(2d kappa_min + sigma)/(2d + sigma), (2d kappa_max + sigma)/(2d + sigma)]
+ * (SRJ_ERR_BAD_SCHEDULE if the operator is not positive definite or the scheme
+ * does not contract).  The mask is copied.  Residual norms count active points
+ * only.  Blocked sweeps implement the plain operator, so a mask or shift sets
+ * the temporal depth to 1.  srj_gradient's boundary gradient covers the ghost
+ * layer only (not the fixed points of a mask).
+ */
+int srj_plan_set_operator(srj_plan_t plan, double sigma, const unsigned char *mask, void *stream);
+
 /* srj_plan_order -- copy the M level indices of the cycle order to order_out (host). */
 int srj_plan_order(srj_plan_t plan, int32_t *order_out);
 

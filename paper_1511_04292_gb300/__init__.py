@@ -114,6 +114,18 @@ class Plan:
         check(self._lib.srj_plan_temporal_depth(self._h, ctypes.byref(T)))
         return T.value
 
+    def set_operator(self, sigma=0.0, mask=None, stream=None):
+        """A = (2d + sigma) I - neighbours on the active points of mask (uint8 CUDA
+        tensor in the padded shape, nonzero = active; None = all interior points)."""
+        import torch
+        mp = None
+        if mask is not None:
+            if not isinstance(mask, torch.Tensor) or not mask.is_cuda or mask.dtype != torch.uint8 \
+                    or tuple(mask.shape) != self.shape or not mask.is_contiguous():
+                raise TypeError("mask must be a contiguous uint8 CUDA tensor of shape %s" % (self.shape,))
+            mp = ctypes.c_void_p(mask.data_ptr())
+        check(self._lib.srj_plan_set_operator(self._h, float(sigma), mp, _stream_ptr(stream)))
+
     def set_sweep_variant(self, v):
         """0: one block per tile; 1: persistent blocks with cp.async prefetch (2-D mixed plans)."""
         check(self._lib.srj_plan_set_sweep_variant(self._h, int(v)))

@@ -105,6 +105,7 @@ SIGNATURES = {
     "srj_plan_set_temporal_depth": (_I, [_VP, _I]),
     "srj_plan_temporal_depth": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "srj_plan_set_sweep_variant": (_I, [_VP, _I]),
+    "srj_plan_set_operator": (_I, [_VP, _D, _VP, _VP]),
     "srj_plan_sweep_variant": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "srj_plan_autotune": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "srj_solve": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),

@@ -44,22 +44,26 @@ cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, doubl
 
 // One FP64 weighted-Jacobi step, fixed operation order, no FMA.
 //   uout = uin + c * ((sum nbrs(uin) + b) - 2d uin)    (interior only)
+// two_d: the diagonal 2d + sigma of a shifted operator (0 = plain 2d); mask:
+// padded uint8 array, 0 = point held fixed (NULL = all interior points active).
 cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b,
-                             double c, cudaStream_t s);
+                             double c, cudaStream_t s, double two_d = 0.0, const unsigned char* mask = nullptr);
 
 // Fused residual r = (h2 * src + sum nbrs(u)) - 2d u on the interior, with L2 /
 // max norms reduced into ns.result.  Optional outputs: r64 (padded float64,
 // interior only), r32 (pitched float32, value r * scale).
 cudaError_t launch_residual(const Geom& g, const double* u, const double* src, double h2,
-                            double* r64, float* r32, double scale, NormScratch ns, cudaStream_t s);
+                            double* r64, float* r32, double scale, NormScratch ns, cudaStream_t s,
+                            double two_d = 0.0, const unsigned char* mask = nullptr);
 
 // One FP32 weighted-Jacobi step on the pitched float32 layout:
 //   eout = ein + c * ((sum nbrs(ein) + r) - 2d ein)    (interior only)
 cudaError_t launch_sweep_f32(const Geom& g, const float* ein, float* eout, const float* r,
-                             float c, cudaStream_t s);
+                             float c, cudaStream_t s, float two_d = 0.0f, const unsigned char* mask = nullptr);
 
 // u (float64 padded, interior) += inv_scale * e (float32 pitched).
-cudaError_t launch_update(const Geom& g, double* u, const float* e, double inv_scale, cudaStream_t s);
+cudaError_t launch_update(const Geom& g, double* u, const float* e, double inv_scale, cudaStream_t s,
+                          const unsigned char* mask = nullptr);
 
 // Layout conversions used by srj_steps on mixed plans.
 cudaError_t launch_to_f32(const Geom& g, const double* u, float* e, cudaStream_t s);          // all points

@@ -48,16 +48,16 @@ __global__ void k_scale_source(Geom g, double h2, const double* __restrict__ f, 
 template <int ND>
 __global__ void __launch_bounds__(kThreads)
 k_sweep_f64(Geom g, const double* __restrict__ uin, double* __restrict__ uout,
-            const double* __restrict__ b, double c) {
+            const double* __restrict__ b, double c, double two_d, const unsigned char* __restrict__ mask) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x + 1;
     const int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
     if (x > g.nx || y > g.ny) return;
-    const double two_d = 2.0 * ND;
     const int zlo = (ND == 3) ? 1 : 0;
     const int zhi = (ND == 3) ? g.nz : 0;
     for (int z = zlo + blockIdx.z; z <= zhi; z += gridDim.z) {
         const int64_t p = idx64(g, x, y, z);
         const double uc = uin[p];
+        if (mask && !mask[p]) { uout[p] = uc; continue; }
         double s = __dadd_rn(uin[p - 1], uin[p + 1]);
         s = __dadd_rn(s, uin[p - g.sx64]);
         s = __dadd_rn(s, uin[p + g.sx64]);
@@ -99,10 +99,10 @@ __device__ inline void block_reduce(double& ss, double& mx, double* sh_ss, doubl
 template <int ND>
 __global__ void __launch_bounds__(kThreads)
 k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src, double h2,
-           double* __restrict__ r64, float* __restrict__ r32, double scale, NormScratch ns) {
+           double* __restrict__ r64, float* __restrict__ r32, double scale, NormScratch ns, double two_d,
+           const unsigned char* __restrict__ mask) {
     __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
     __shared__ bool last;
-    const double two_d = 2.0 * ND;
     double ss = 0.0, mx = 0.0;
     const int64_t rows = (int64_t)g.ny * (ND == 3 ? g.nz : 1);
     for (int64_t rr = blockIdx.x; rr < rows; rr += gridDim.x) {
@@ -111,6 +111,10 @@ k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src,
         const int64_t base = idx64(g, 0, y, z);
         for (int x = threadIdx.x + 1; x <= g.nx; x += blockDim.x) {
             const int64_t p = base + x;
+            if (mask && !mask[p]) {
+                if (r32) r32[idx32(g, x, y, z)] = 0.0f;
+                continue;
+            }
             const double uc = u[p];
             double s = __dadd_rn(u[p - 1], u[p + 1]);
             s = __dadd_rn(s, u[p - g.sx64]);
@@ -159,11 +163,10 @@ k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src,
 template <int ND>
 __global__ void __launch_bounds__(kThreads)
 k_sweep_f32(Geom g, const float* __restrict__ ein, float* __restrict__ eout,
-            const float* __restrict__ r, float c) {
+            const float* __restrict__ r, float c, float two_d, const unsigned char* __restrict__ mask) {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);  // 0-based interior x
     const int y = blockIdx.y * blockDim.y + threadIdx.y + 1;
     if (x0 >= g.nx || y > g.ny) return;
-    const float two_d = 2.0f * ND;
     const int zlo = (ND == 3) ? 1 : 0;
     const int zhi = (ND == 3) ? g.nz : 0;
     for (int z = zlo + blockIdx.z; z <= zhi; z += gridDim.z) {
@@ -189,6 +192,13 @@ k_sweep_f32(Geom g, const float* __restrict__ ein, float* __restrict__ eout,
         o.y = fmaf(c, fmaf(-two_d, cc.y, nb.y + rr.y), cc.y);
         o.z = fmaf(c, fmaf(-two_d, cc.z, nb.z + rr.z), cc.z);
         o.w = fmaf(c, fmaf(-two_d, cc.w, nb.w + rr.w), cc.w);
+        if (mask) {  // inactive points keep their value
+            const int64_t q = idx64(g, x0 + 1, y, z);
+            if (!mask[q]) o.x = cc.x;
+            if (x0 + 1 < g.nx && !mask[q + 1]) o.y = cc.y;
+            if (x0 + 2 < g.nx && !mask[q + 2]) o.z = cc.z;
+            if (x0 + 3 < g.nx && !mask[q + 3]) o.w = cc.w;
+        }
         if (x0 + 4 <= g.nx) {
             *reinterpret_cast<float4*>(eout + p) = o;
         } else {
@@ -211,10 +221,11 @@ __device__ inline bool decode(const Geom& g, int64_t i, int& x, int& y, int& z) 
     return x >= 1 && x <= g.nx && y >= 1 && y <= g.ny && (g.nd == 2 || (z >= 1 && z <= g.nz));
 }
 
-__global__ void k_update(Geom g, double* __restrict__ u, const float* __restrict__ e, double inv_scale) {
+__global__ void k_update(Geom g, double* __restrict__ u, const float* __restrict__ e, double inv_scale,
+                         const unsigned char* __restrict__ mask) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n64; i += (int64_t)gridDim.x * blockDim.x) {
         int x, y, z;
-        if (decode(g, i, x, y, z)) u[i] += inv_scale * (double)e[idx32(g, x, y, z)];
+        if (decode(g, i, x, y, z) && (!mask || mask[i])) u[i] += inv_scale * (double)e[idx32(g, x, y, z)];
     }
 }
 
@@ -331,35 +342,40 @@ cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, doubl
 }
 
 cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b, double c,
-                             cudaStream_t s) {
+                             cudaStream_t s, double two_d, const unsigned char* mask) {
+    if (two_d == 0.0) two_d = 2.0 * g.nd;
     dim3 blk(64, 4, 1);
     dim3 grd((g.nx + 63) / 64, (g.ny + 3) / 4, g.nd == 3 ? (unsigned)std::min(g.nz, 65535) : 1u);
-    if (g.nd == 3) k_sweep_f64<3><<<grd, blk, 0, s>>>(g, uin, uout, b, c);
-    else           k_sweep_f64<2><<<grd, blk, 0, s>>>(g, uin, uout, b, c);
+    if (g.nd == 3) k_sweep_f64<3><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+    else           k_sweep_f64<2><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const Geom& g, const double* u, const double* src, double h2, double* r64,
-                            float* r32, double scale, NormScratch ns, cudaStream_t s) {
+                            float* r32, double scale, NormScratch ns, cudaStream_t s, double two_d,
+                            const unsigned char* mask) {
+    if (two_d == 0.0) two_d = 2.0 * g.nd;
     const int64_t rows = (int64_t)g.ny * (g.nd == 3 ? g.nz : 1);
     const int blocks = (int)std::min<int64_t>(rows, kMaxNormBlocks);
-    if (g.nd == 3) k_residual<3><<<blocks, kThreads, 0, s>>>(g, u, src, h2, r64, r32, scale, ns);
-    else           k_residual<2><<<blocks, kThreads, 0, s>>>(g, u, src, h2, r64, r32, scale, ns);
+    if (g.nd == 3) k_residual<3><<<blocks, kThreads, 0, s>>>(g, u, src, h2, r64, r32, scale, ns, two_d, mask);
+    else           k_residual<2><<<blocks, kThreads, 0, s>>>(g, u, src, h2, r64, r32, scale, ns, two_d, mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_f32(const Geom& g, const float* ein, float* eout, const float* r, float c,
-                             cudaStream_t s) {
+                             cudaStream_t s, float two_d, const unsigned char* mask) {
+    if (two_d == 0.0f) two_d = 2.0f * g.nd;
     const int quads = (g.nx + 3) / 4;
     dim3 blk(64, 4, 1);
     dim3 grd((quads + 63) / 64, (g.ny + 3) / 4, g.nd == 3 ? (unsigned)std::min(g.nz, 65535) : 1u);
-    if (g.nd == 3) k_sweep_f32<3><<<grd, blk, 0, s>>>(g, ein, eout, r, c);
-    else           k_sweep_f32<2><<<grd, blk, 0, s>>>(g, ein, eout, r, c);
+    if (g.nd == 3) k_sweep_f32<3><<<grd, blk, 0, s>>>(g, ein, eout, r, c, two_d, mask);
+    else           k_sweep_f32<2><<<grd, blk, 0, s>>>(g, ein, eout, r, c, two_d, mask);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(const Geom& g, double* u, const float* e, double inv_scale, cudaStream_t s) {
-    k_update<<<grid_for(g.n64), kThreads, 0, s>>>(g, u, e, inv_scale);
+cudaError_t launch_update(const Geom& g, double* u, const float* e, double inv_scale, cudaStream_t s,
+                          const unsigned char* mask) {
+    k_update<<<grid_for(g.n64), kThreads, 0, s>>>(g, u, e, inv_scale, mask);
     return cudaGetLastError();
 }
 

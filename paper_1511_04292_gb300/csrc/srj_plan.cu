@@ -247,6 +247,9 @@ struct srj_plan {
 
     // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
     int tdepth = 1;
+    double sigma = 0.0;              // diagonal shift: A = (2d + sigma) I - neighbours
+    double diag64 = 0.0;             // 2d + sigma
+    unsigned char* mask = nullptr;   // plan-owned copy of the activity mask (NULL: all active)
     int variant = 0;     // blocked sweep: 0 = one block per tile, 1 = persistent with cp.async prefetch
     int sm_count = 152;
     float* e_final = nullptr;  // buffer holding the correction after one cycle
@@ -266,6 +269,7 @@ struct srj_plan {
         cudaFree(ea); cudaFree(eb); cudaFree(r32);
         cudaFree(ns.partials); cudaFree(ns.counter); cudaFree(ns.result);
         cudaFree(d_err);
+        cudaFree(mask);
         if (host_norms) cudaFreeHost(host_norms);
         if (host_err) cudaFreeHost(host_err);
     }
@@ -284,7 +288,7 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
     for (int64_t k = 0; k < count && err == cudaSuccess;) {
         const int n = (int)std::min<int64_t>(T, count - k);
         if (T == 1) {
-            err = srj::launch_sweep_f32(p->g, in, out, p->r32, (float)p->c64[(size_t)((first + k) % M)], s);
+            err = srj::launch_sweep_f32(p->g, in, out, p->r32, (float)p->c64[(size_t)((first + k) % M)], s, (float)p->diag64, p->mask);
         } else {
             srj::TbSteps st{};
             st.T = n;
@@ -308,7 +312,7 @@ int capture_cycle(srj_plan* p, int start) {
         for (int64_t k = 0; k < p->M && err == cudaSuccess; ++k) {
             const bool from_a = ((k + start) % 2) == 0;
             err = srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
-                                        p->c64[(size_t)k], p->cap);
+                                        p->c64[(size_t)k], p->cap, p->diag64, p->mask);
         }
     } else {
         err = cudaMemsetAsync(p->ea, 0, sizeof(float) * (size_t)p->g.n32, p->cap);
@@ -357,6 +361,8 @@ int set_depth(srj_plan* p, int T) {
     if (T < 1 || T > srj::tb_max_steps()) return fail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..%d", srj::tb_max_steps());
     if (T > 1 && !(p->precision == SRJ_PREC_MIXED && p->g.nd == 2))
         return fail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for 2-D mixed-precision plans");
+    if (T > 1 && (p->mask || p->sigma != 0.0))
+        return fail(SRJ_ERR_INVALID_ARG, "temporal blocking implements the plain operator (no mask, no shift)");
     p->tdepth = T;
     return recapture(p);
 }
@@ -472,8 +478,9 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
                              "cycle order amplifies FP32 rounding by 10^%.1f inside a cycle (limit 10^%.0f); "
                              "use another order or FP64", sg, kMaxSuffixGrowthFP32));
     }
+    p->diag64 = (double)(2 * ndim);
     p->c64.resize((size_t)M);
-    for (int64_t k = 0; k < M; ++k) p->c64[(size_t)k] = p->omega[p->order[(size_t)k]] / (double)(2 * ndim);
+    for (int64_t k = 0; k < M; ++k) p->c64[(size_t)k] = p->omega[p->order[(size_t)k]] / p->diag64;
 
     if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(SRJ_ERR_CUDA, "no CUDA device"));
     auto alloc = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes) == cudaSuccess; };
@@ -534,6 +541,38 @@ int srj_plan_set_temporal_depth(srj_plan_t plan, int T) {
     return set_depth(plan, T);
 }
 
+int srj_plan_set_operator(srj_plan_t p, double sigma, const unsigned char* mask, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    const int nd = p->g.nd;
+    const double diag = (double)(2 * nd) + sigma;
+    if (!std::isfinite(sigma) || !(diag > 0.0)) return fail(SRJ_ERR_INVALID_ARG, "need 2d + sigma > 0");
+    // spectrum of D^-1 A for the shifted operator; a mask selects a principal
+    // submatrix, whose eigenvalues lie in the same range (Cauchy interlacing)
+    const double km = ((double)(2 * nd) * p->kappa_min + sigma) / diag;
+    const double kx = ((double)(2 * nd) * p->kappa_max + sigma) / diag;
+    if (!(km > 0.0)) return fail(SRJ_ERR_BAD_SCHEDULE, "shifted operator is not positive definite on this grid");
+    const double gmax = km < kx ? max_cycle_log10(p->omega, p->q, km, kx) : cycle_log10(p->omega, p->q, km);
+    if (!(gmax < 0.0))
+        return fail(SRJ_ERR_BAD_SCHEDULE, "integer scheme does not contract on the shifted spectrum [%.6g, %.6g]", km, kx);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mask) {
+        if (!p->mask) SRJ_CUDA(cudaMalloc((void**)&p->mask, (size_t)p->g.n64));
+        SRJ_CUDA(cudaMemcpyAsync(p->mask, mask, (size_t)p->g.n64, cudaMemcpyDeviceToDevice, s));
+        SRJ_CUDA(cudaStreamSynchronize(s));
+    } else if (p->mask) {
+        SRJ_CUDA(cudaFree(p->mask));
+        p->mask = nullptr;
+    }
+    p->sigma = sigma;
+    p->diag64 = diag;
+    p->gmax = gmax;
+    for (int64_t k = 0; k < p->M; ++k) p->c64[(size_t)k] = p->omega[p->order[(size_t)k]] / diag;
+    // the blocked kernels implement the plain operator only
+    if (p->mask || sigma != 0.0) p->tdepth = 1;
+    return recapture(p);
+}
+
 int srj_plan_set_sweep_variant(srj_plan_t plan, int v) {
     int rc = check_plan(plan);
     if (rc) return rc;
@@ -561,7 +600,7 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     // candidates (T, variant): the unblocked sweep, then both blocked variants for T = 2..8
     int candT[22] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
     int candV[22] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2};
-    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2) ? 22 : 1;
+    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2 && !p->mask && p->sigma == 0.0) ? 22 : 1;
     int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;
@@ -579,7 +618,7 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
                 for (int64_t k = 0; k < steps; ++k) {
                     const bool a = (k % 2) == 0;
                     SRJ_CUDA(srj::launch_sweep_f64(p->g, a ? p->ua : p->ub, a ? p->ub : p->ua, p->b,
-                                                   p->c64[(size_t)(k % p->M)], s));
+                                                   p->c64[(size_t)(k % p->M)], s, p->diag64, p->mask));
                 }
             }
             SRJ_CUDA(cudaEventRecord(p->ev1, s));
@@ -620,7 +659,7 @@ int srj_residual(srj_plan_t p, const double* f, const double* u, double* r_out, 
     if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (r_out) SRJ_CUDA(cudaMemsetAsync(r_out, 0, sizeof(double) * (size_t)p->g.n64, s));
-    SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, r_out, nullptr, 1.0, p->ns, s));
+    SRJ_CUDA(srj::launch_residual(p->g, u, f, p->h2, r_out, nullptr, 1.0, p->ns, s, p->diag64, p->mask));
     double a, bb;
     rc = read_norms(p, s, &a, &bb);
     if (rc) return rc;
@@ -644,7 +683,7 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
         for (int64_t k = 0; k < count; ++k) {
             const bool from_a = (k % 2) == 0;
             SRJ_CUDA(srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
-                                           p->c64[(size_t)((first + k) % M)], s));
+                                           p->c64[(size_t)((first + k) % M)], s, p->diag64, p->mask));
         }
         SRJ_CUDA(cudaMemcpyAsync(u, (count % 2) ? p->ub : p->ua, by, cudaMemcpyDeviceToDevice, s));
     } else {
@@ -707,11 +746,11 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
         SRJ_CUDA(cudaMemcpyAsync(p->ua, u, by64, cudaMemcpyDeviceToDevice, s));
         SRJ_CUDA(cudaMemcpyAsync(p->ub, u, by64, cudaMemcpyDeviceToDevice, s));
         SRJ_CUDA(srj::launch_scale_source(p->g, h2, f, p->b, s));
-        SRJ_CUDA(srj::launch_residual(p->g, p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s));
+        SRJ_CUDA(srj::launch_residual(p->g, p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s, p->diag64, p->mask));
     } else {
         const size_t by32 = sizeof(float) * (size_t)p->g.n32;
         SRJ_CUDA(cudaMemsetAsync(p->eb, 0, by32, s));  // ghosts of the corrections are 0
-        SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, nullptr, 1.0, p->ns, s));
+        SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, nullptr, 1.0, p->ns, s, p->diag64, p->mask));
     }
     if ((rc = read_norms(p, s, &l2, &linf))) return rc;
     st.residual_checks = 1;
@@ -728,7 +767,7 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
             int ex = 0;
             std::frexp(linf, &ex);
             scale = std::ldexp(1.0, -ex);
-            SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s));
+            SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s, p->diag64, p->mask));
         }
         double best = st.r0_l2;
         int stall = 0;
@@ -738,12 +777,12 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
                 SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[p->M % 2 ? cur : 0], s));
                 SRJ_CUDA(cudaEventRecord(p->ev1, s));
                 if (p->M % 2) cur ^= 1;
-                SRJ_CUDA(srj::launch_residual(p->g, cur ? p->ub : p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s));
+                SRJ_CUDA(srj::launch_residual(p->g, cur ? p->ub : p->ua, p->b, 1.0, nullptr, nullptr, 1.0, p->ns, s, p->diag64, p->mask));
             } else {
                 SRJ_CUDA(cudaGraphLaunch(p->cycle_exec[0], s));
                 SRJ_CUDA(cudaEventRecord(p->ev1, s));
-                SRJ_CUDA(srj::launch_update(p->g, u, p->e_final, 1.0 / scale, s));
-                SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s));
+                SRJ_CUDA(srj::launch_update(p->g, u, p->e_final, 1.0 / scale, s, p->mask));
+                SRJ_CUDA(srj::launch_residual(p->g, u, f, h2, nullptr, p->r32, scale, p->ns, s, p->diag64, p->mask));
             }
             if ((rc = read_norms(p, s, &l2, &linf))) return rc;
             float ms = 0.f;
