@@ -37,16 +37,19 @@ __device__ inline float upd(float c, float two_d, float cc, float nb, float rr) 
 // (float4, 4 consecutive columns per lane) and the defect rr[i].  Only the
 // band's top and bottom rows cross warps, through a double-buffered shared
 // slot, so each step costs one barrier and four shared-memory accesses per lane.
-template <int T, bool MASKED, int W = kWarps>
+// MY: some rows of the tile lie outside 1..ny (iny[] is uniform over the warp);
+// MX: some columns lie outside 1..nx.  Those points keep their value.
+template <int T, bool MY, bool MX, int W = kWarps>
 __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr)[kBand], float4* xch,
                                            const float (&cs)[8], int n, int lane, int w, const bool (&inx)[4],
                                            const bool (&iny)[kBand]) {
     const float two_d = 4.0f;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 m4 = make_float2(-two_d, -two_d);
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        if (t >= n) break;  // n is uniform over the block
-        const float c = cs[t];
+        if (t >= n) break;  // n is uniform over the block (T when known at compile time)
+        const float2 cv = make_float2(cs[t], cs[t]);
         float4* slot = xch + (t & 1) * (2 * W * 32);
         slot[(2 * w) * 32 + lane] = e[0];              // top row of this band
         slot[(2 * w + 1) * 32 + lane] = e[kBand - 1];  // bottom row
@@ -62,14 +65,14 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
             // stale halo of the tile, so what they compute is never stored
             const float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
             const float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            // Packed FP32x2 form of the single-step update: per component the
-            // same operations in the same order as upd() with
-            // nb = ((left + right) + up) + down (x,y pair and z,w pair).
-            const float2 m4 = make_float2(-two_d, -two_d);
-            const float2 cv = make_float2(c, c);
-            const float2 mid = make_float2(cur.y, cur.z);
-            float2 s0 = __fadd2_rn(make_float2(lf, cur.x), mid);    // (lf + y, x + z)
-            float2 s1 = __fadd2_rn(mid, make_float2(cur.w, rt));    // (y + w, z + rt)
+            // Single-step update in FP32x2 form: per component the same
+            // operations in the same order as upd() with
+            // nb = ((left + right) + up) + down.  The left + right sums are
+            // scalar adds whose results land directly in the (x,y) / (z,w)
+            // pairs; pairing the misaligned neighbours for a packed add would
+            // cost more register moves than the adds it saves.
+            float2 s0 = make_float2(lf + cur.y, cur.x + cur.z);
+            float2 s1 = make_float2(cur.y + cur.w, cur.z + rt);
             s0 = __fadd2_rn(s0, make_float2(up.x, up.y));
             s1 = __fadd2_rn(s1, make_float2(up.z, up.w));
             s0 = __fadd2_rn(s0, make_float2(dn.x, dn.y));
@@ -80,12 +83,13 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
             const float2 o0 = __ffma2_rn(cv, __ffma2_rn(m4, c0, s0), c0);
             const float2 o1 = __ffma2_rn(cv, __ffma2_rn(m4, c1, s1), c1);
             float4 o = make_float4(o0.x, o0.y, o1.x, o1.y);
-            if (MASKED) {
-                o.x = (iny[i] && inx[0]) ? o.x : cur.x;
-                o.y = (iny[i] && inx[1]) ? o.y : cur.y;
-                o.z = (iny[i] && inx[2]) ? o.z : cur.z;
-                o.w = (iny[i] && inx[3]) ? o.w : cur.w;
+            if (MX) {
+                o.x = inx[0] ? o.x : cur.x;
+                o.y = inx[1] ? o.y : cur.y;
+                o.z = inx[2] ? o.z : cur.z;
+                o.w = inx[3] ? o.w : cur.w;
             }
+            if (MY && !iny[i]) o = cur;
             up = cur;
             e[i] = o;
         }
@@ -108,6 +112,10 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
     const int w = threadIdx.x >> 5;
     const int X0 = 1 + TX * bx - HX;
     const int Y0 = 1 + TY * by - T;
+    const int Yw = Y0 + w * kBand;  // this warp's first row
+    // a tile whose every point is an interior grid point needs no masks
+    const bool xin = X0 >= 1 && X0 + kSX - 1 <= nx;
+    const bool yin = Y0 >= 1 && Y0 + SY - 1 <= ny;
 
     // Band fill: float4 loads of e and r straight into registers.  The float32
     // column of padded x is x + 3, a multiple of 4 here, so each float4 lies
@@ -119,7 +127,7 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
     bool iny[kBand];
 #pragma unroll
     for (int i = 0; i < kBand; ++i) {
-        const int64_t y = (int64_t)Y0 + w * kBand + i;
+        const int64_t y = (int64_t)Yw + i;
         e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         rr[i] = e[i];
         if (colok && y >= 0 && y < rows) {
@@ -135,10 +143,10 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
         const int x = X0 + 4 * lane + j;
         inx[j] = x >= 1 && x <= nx;
     }
-    // tiles whose every point is an interior grid point need no masking
-    const bool interior = X0 >= 1 && X0 + kSX - 1 <= nx && Y0 >= 1 && Y0 + SY - 1 <= ny;
-    if (interior) band_steps<T, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
-    else          band_steps<T, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
+    if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
+    else if (xin)   band_steps<T, true, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
+    else if (yin)   band_steps<T, false, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
+    else            band_steps<T, true, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
 
     // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
@@ -162,14 +170,95 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
     }
 }
 
+// Single grid, n = T steps per launch.  Same tile as tile_sweep; interior
+// tiles (the vast majority) load and store without bounds checks.  (Kept as its
+// own body: routed through tile_sweep, this form costs the compiler hundreds of
+// bytes of register spills.)
 template <int T, int W>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
                TbSteps steps) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int SY = W * kBand;
+    constexpr int TX = kSX - 2 * HX, TY = SY - 2 * T;
     __shared__ float4 xch[2 * 2 * W * 32];  // [slot][warp][top/bottom][lane]
-    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
-    tile_sweep<T, W>(ein, rin, eout, g.nx, g.ny, g.p32, rows, steps.c, steps.T, (int)blockIdx.x, (int)blockIdx.y,
-                     false, xch);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int X0 = 1 + TX * (int)blockIdx.x - HX, Y0 = 1 + TY * (int)blockIdx.y - T;
+    const int Yw = Y0 + w * kBand;  // this warp's first row
+    const bool xin = X0 >= 1 && X0 + kSX - 1 <= g.nx;
+    const bool yin = Y0 >= 1 && Y0 + SY - 1 <= g.ny;
+    const int64_t base = (int64_t)Yw * g.p32 + X0 + 3 + 4 * lane;  // this lane's float4 of row Yw
+    float4 e[kBand], rr[kBand];
+    bool iny[kBand];
+    if (xin && yin) {
+        const float4* pe = reinterpret_cast<const float4*>(ein + base);
+        const float4* pr = reinterpret_cast<const float4*>(rin + base);
+        const int64_t stride = g.p32 / 4;  // p32 is a multiple of 32
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            e[i] = __ldg(pe + i * stride);
+            rr[i] = __ldg(pr + i * stride);
+            iny[i] = true;
+        }
+    } else {
+        // float32 column of padded x is x + 3, a multiple of 4 here: each
+        // float4 lies wholly inside or outside the buffer; outside reads as 0
+        const int col = X0 + 3 + 4 * lane;
+        const bool colok = col >= 0 && col + 4 <= g.p32;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int64_t y = (int64_t)Yw + i;
+            e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rr[i] = e[i];
+            if (colok && y >= 0 && y < (int64_t)g.ny + 2) {
+                const int64_t off = y * g.p32 + col;
+                e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+                rr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
+            }
+            iny[i] = y >= 1 && y <= g.ny;
+        }
+    }
+    bool inx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int x = X0 + 4 * lane + j;
+        inx[j] = x >= 1 && x <= g.nx;
+    }
+    if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+    else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+    else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+    else            band_steps<T, true, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+
+    // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
+    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+    if (lane < lane_lo || lane >= lane_hi) return;
+    if (xin && yin) {
+        float4* po = reinterpret_cast<float4*>(eout + base);
+        const int64_t stride = g.p32 / 4;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            if (row >= T && row < T + TY) po[i * stride] = e[i];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kBand; ++i) {
+        const int row = w * kBand + i;
+        if (row < T || row >= T + TY) continue;
+        const int y = Y0 + row;
+        if (y < 1 || y > g.ny) continue;
+        const int x = X0 + 4 * lane;
+        float* dst = eout + (int64_t)y * g.p32 + x + 3;  // 16-byte aligned
+        if (inx[0] && inx[3]) {
+            *reinterpret_cast<float4*>(dst) = e[i];
+        } else {
+            if (inx[0]) dst[0] = e[i].x;
+            if (inx[1]) dst[1] = e[i].y;
+            if (inx[2]) dst[2] = e[i].z;
+            if (inx[3]) dst[3] = e[i].w;
+        }
+    }
 }
 
 __device__ inline void cp_async16(void* smem_dst, const void* gsrc, unsigned src_bytes) {
@@ -238,9 +327,12 @@ k_sweep_f32_tbp(const float* __restrict__ ein, const float* __restrict__ rin, fl
             const int x = X0 + 4 * lane + j;
             inx[j] = x >= 1 && x <= g.nx;
         }
-        const bool interior = X0 >= 1 && X0 + kSX - 1 <= g.nx && Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
-        if (interior) band_steps<T, false>(e, rr, xch, steps.c, steps.T, lane, w, inx, iny);
-        else          band_steps<T, true>(e, rr, xch, steps.c, steps.T, lane, w, inx, iny);
+        const bool xin = X0 >= 1 && X0 + kSX - 1 <= g.nx;
+        const bool yin = Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
+        if (xin && yin) band_steps<T, false, false>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else if (xin)   band_steps<T, true, false>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else if (yin)   band_steps<T, false, true>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else            band_steps<T, true, true>(e, rr, xch, steps.c, T, lane, w, inx, iny);
         const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
         if (lane >= lane_lo && lane < lane_hi) {
 #pragma unroll

@@ -248,7 +248,7 @@ def test_full_size_workload2_mixed_solve():
 
 @pytest.mark.parametrize("dims", [(37, 23), (130, 67), (1, 1), (5, 300), (129, 129), (300, 5), (1000, 700)])
 def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
-    """Temporal blocking (T steps per launch from a shared-memory tile) must give
+    """Temporal blocking (T steps per launch on register-resident tiles) must give
     exactly the bits of T single-step launches, for every T, for step counts that
     are not multiples of T, and on grids smaller or ragged against the tile."""
     omega, q, order = small_schedule(dims, 4)
