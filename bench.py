@@ -61,6 +61,7 @@ def parse():
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
+    ap.add_argument("--ndim", type=int, default=2, choices=[2, 3], help="kernel-case: grid dimension (n^ndim points)")
     ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
     ap.add_argument("--variant", type=int, default=None, help="kernel-case f32: blocked sweep variant (0 or 1)")
     return ap.parse_args()
@@ -72,16 +73,17 @@ def run_kernel_case(args):
     import srj_workloads as W
     n = args.n
     torch.cuda.set_device(0)
-    plan = srj.Plan((n, n), 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
+    dims = (n,) * args.ndim
+    plan = srj.Plan(dims, 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
     if args.T is not None:
         plan.set_temporal_depth(args.T)
     if args.variant is not None:
         plan.set_sweep_variant(args.variant)
-    f = torch.from_numpy(W.random_field((n, n), 1)).cuda()
-    u = torch.from_numpy(W.random_field((n, n), 2)).cuda()
+    f = torch.from_numpy(W.random_field(dims, 1)).cuda()
+    u = torch.from_numpy(W.random_field(dims, 2)).cuda()
     plan.steps(f, u, 0, args.count)
     torch.cuda.synchronize()
-    print("kernel case %s n=%d count=%d done" % (args.kernel_case, n, args.count))
+    print("kernel case %s n=%d^%d count=%d done" % (args.kernel_case, n, args.ndim, args.count))
     return 0
 
 
@@ -180,8 +182,9 @@ def secondary_workloads(stream):
     ms = a.elapsed_time(b)
     out["3d_poisson_512^3_P12_mixed_tol1e-9"] = {
         "time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * n ** 3 / (ms / 1e3) / 1e9,
-        "cycles": st["cycles"], "final_rel_residual": st["rel_res"], "sweep_kernel": "k_sweep_f32<3> (unblocked)",
-        "sweep_kernel_gbs": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
+        "cycles": st["cycles"], "final_rel_residual": st["rel_res"], "temporal_depth": plan.temporal_depth(),
+        "sweep_kernel": "k_sweep3_f32_tb2 (2 steps per launch)" if plan.temporal_depth() == 2 else "k_sweep_f32<3>",
+        "effective_gbs_per_step": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
     del f, u0, u, plan
     torch.cuda.empty_cache()
     # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10

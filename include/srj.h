@@ -122,11 +122,13 @@ int srj_plan_destroy(srj_plan_t plan);
 int srj_plan_info(srj_plan_t plan, int64_t *M, double *kappa_min, double *log10_cycle_factor_max);
 
 /*
- * srj_plan_set_temporal_depth -- number T (1..8) of consecutive FP32 steps that
- * one sweep launch applies to a tile held in shared memory (temporal blocking;
- * T = 1 is the plain one-step sweep).  Available for 2-D mixed-precision plans
- * (default 4); every other plan accepts only T = 1.  T blocked steps give the
- * same bits as T single steps.  Re-captures the plan's cycle graph.
+ * srj_plan_set_temporal_depth -- number T of consecutive FP32 steps that one
+ * sweep launch applies per HBM round trip (temporal blocking; T = 1 is the
+ * plain one-step sweep).  2-D mixed-precision plans: T = 1..8 on register-
+ * resident tiles (default 4).  3-D mixed-precision plans: T = 1 or 2, tiles
+ * streamed through z (default 2).  FP64 plans and plans with a mask or shift
+ * accept only T = 1.  T blocked steps give the same bits as T single steps.
+ * Re-captures the plan's cycle graph.
  */
 int srj_plan_set_temporal_depth(srj_plan_t plan, int T);
 

@@ -16,7 +16,7 @@ _ROOT = _PKG.parent
 _CSRC = _PKG / "csrc"
 _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
-SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
+SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_tblock3.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -287,8 +287,11 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
     const int T = p->tdepth;
     for (int64_t k = 0; k < count && err == cudaSuccess;) {
         const int n = (int)std::min<int64_t>(T, count - k);
-        if (T == 1) {
+        if (T == 1 || n == 1) {
             err = srj::launch_sweep_f32(p->g, in, out, p->r32, (float)p->c64[(size_t)((first + k) % M)], s, (float)p->diag64, p->mask);
+        } else if (p->g.nd == 3) {  // 3-D: two steps per launch
+            err = srj::launch_sweep3_f32_tb2(p->g, in, p->r32, out, (float)p->c64[(size_t)((first + k) % M)],
+                                             (float)p->c64[(size_t)((first + k + 1) % M)], p->sm_count, s);
         } else {
             srj::TbSteps st{};
             st.T = n;
@@ -359,8 +362,9 @@ int recapture(srj_plan* p) {
 
 int set_depth(srj_plan* p, int T) {
     if (T < 1 || T > srj::tb_max_steps()) return fail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..%d", srj::tb_max_steps());
-    if (T > 1 && !(p->precision == SRJ_PREC_MIXED && p->g.nd == 2))
-        return fail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for 2-D mixed-precision plans");
+    if (T > 1 && p->precision != SRJ_PREC_MIXED)
+        return fail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for mixed-precision plans");
+    if (T > 2 && p->g.nd == 3) return fail(SRJ_ERR_INVALID_ARG, "3-D plans take temporal depth 1 or 2");
     if (T > 1 && (p->mask || p->sigma != 0.0))
         return fail(SRJ_ERR_INVALID_ARG, "temporal blocking implements the plain operator (no mask, no shift)");
     p->tdepth = T;
@@ -507,12 +511,12 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
         cudaGetLastError();
         return bail(fail(SRJ_ERR_CUDA, "plan setup failed"));
     }
-    if (precision == SRJ_PREC_MIXED && ndim == 2) {
-        if (srj::tb_prepare() != cudaSuccess) {
+    if (precision == SRJ_PREC_MIXED) {
+        if (srj::tb_prepare() != cudaSuccess || srj::tb3_prepare() != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(SRJ_ERR_CUDA, "set-up of the blocked sweep failed"));
         }
-        p->tdepth = 4;
+        p->tdepth = ndim == 2 ? 4 : 2;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) == cudaSuccess && sms > 0)
             p->sm_count = sms;
@@ -597,10 +601,10 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     int rc = check_plan(p);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // candidates (T, variant): the unblocked sweep, then both blocked variants for T = 2..8
+    // candidates (T, variant): the unblocked sweep, then the blocked variants for T = 2..8 (2-D) or T = 2 (3-D)
     int candT[22] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
     int candV[22] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2};
-    int ncand = (p->precision == SRJ_PREC_MIXED && p->g.nd == 2 && !p->mask && p->sigma == 0.0) ? 22 : 1;
+    int ncand = (p->precision == SRJ_PREC_MIXED && !p->mask && p->sigma == 0.0) ? (p->g.nd == 2 ? 22 : 2) : 1;
     int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;
