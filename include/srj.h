@@ -366,6 +366,65 @@ const char *srj_last_error(void);
 /* Library version string. */
 const char *srj_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Spherical-coordinate operators (Sect. 5.2), FP64
+ *
+ * Grid: dims[0] = n_r radial points (fastest), dims[1] = n_theta polar points
+ * [, dims[2] = n_phi azimuthal points], cell centred on r in [0, 1], theta in
+ * [0, pi], phi in [0, 2 pi]: r_i = (i - 1/2) / n_r etc.  Arrays are padded
+ * float64 grids in the layout of srj_solve (one ghost layer per side).
+ * Operator: the Poisson operator in spherical coordinates multiplied by r^2,
+ * with separable coefficients (each array in padded index order):
+ *   (L u)_p = cr_m[i] u(i-1) + cr_p[i] u(i+1) + ct_m[j] u(j-1) + ct_p[j] u(j+1)
+ *             [+ cp[j] (u(k-1) + u(k+1))] - d_p u_p,
+ *   d_p = cr_0[i] + ct_0[j] [+ 2 cp[j]];   radial = cr_m | cr_p | cr_0
+ *   (3 (n_r + 2) doubles), polar = ct_m | ct_p | ct_0 (3 (n_theta + 2)),
+ *   azim = cp (n_theta + 2; 3-D only).
+ * System L u = b (b = r^2 s).  Boundary prescriptions, applied at every step:
+ * the r = 1 ghost layer of u holds Dirichlet data; u_0 = u_1 = u_2 at r = 0 (the
+ * row i = 1 copies row 2, which is iterated with u(i-1) = u(i)); Neumann mirrors
+ * at theta = 0, pi; periodic in phi.  The active points are i = 2..n_r.
+ * Step (Sect. 3.1 with diagonal -d): u' = u + omega ((L u - b) / d).
+ * ------------------------------------------------------------------------- */
+typedef struct srj_sph_plan *srj_sph_plan_t;
+
+/* Host helper: the Sect. 5.2 coefficients for dims (central differences of
+ * r^2 u_rr + 2 r u_r + u_tt + cot(t) u_t [+ u_pp / sin^2 t]):
+ *   cr_m = r (r - dr) / dr^2, cr_p = r (r + dr) / dr^2, cr_0 = 2 r^2 / dr^2,
+ *   ct_m = 1/dt^2 - cot(t) / (2 dt), ct_p = 1/dt^2 + cot(t) / (2 dt),
+ *   ct_0 = 2 / dt^2, cp = 1 / (sin^2(t) dp^2) (polar / azimuthal ghosts 0).
+ * Outputs are host arrays of the sizes above (azim may be NULL in 2-D). */
+int srj_sph_coefficients(int ndim, const int64_t *dims, double *radial, double *polar, double *azim);
+
+/* Build a plan: dims and coefficient arrays (host, copied; finite); the
+ * schedule as in srj_plan_create (order NULL: drift order).  The integer scheme
+ * must contract on [1 / max omega, 2) (SRJ_ERR_BAD_SCHEDULE); the Jacobi-scaled
+ * operator's spectrum lies in (0, 2) for weakly diagonally dominant, irreducible
+ * rows with strict dominance next to the Dirichlet boundary, which the Sect. 5.2
+ * coefficients give. */
+int srj_sph_plan_create(srj_sph_plan_t *plan, int ndim, const int64_t *dims, const double *radial,
+                        const double *polar, const double *azim, int P, const double *omega, const int32_t *q,
+                        const int32_t *order);
+int srj_sph_plan_destroy(srj_sph_plan_t plan);
+
+/* count steps of the cycle order from position first: u (device, in place);
+ * writes the active points and row i = 1, leaves the other ghosts as given. */
+int srj_sph_steps(srj_sph_plan_t plan, const double *b, double *u, int64_t first, int64_t count, void *stream);
+
+/* l2 / linf (host outputs) of res = L u - b over the active points; r_out
+ * (device, may be NULL) gets res there and 0 elsewhere.  Blocks the host. */
+int srj_sph_residual(srj_sph_plan_t plan, const double *b, const double *u, double *r_out, double *l2,
+                     double *linf, void *stream);
+
+/* SRJ cycles until ||res||_2 / ||res_0||_2 <= tol (or max_cycles, divergence,
+ * or a stalled residual: stats->stagnated), then the ghost layer and row i = 1
+ * are set from the prescriptions.  b, u: device; u in place.  Blocks the host. */
+int srj_sph_solve(srj_sph_plan_t plan, const double *b, double *u, double tol, int64_t max_cycles, void *stream,
+                  srj_stats_t *stats);
+
+/* Set the ghost layer and row i = 1 of u (device) from the prescriptions. */
+int srj_sph_finalize(srj_sph_plan_t plan, double *u, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ _ROOT = _PKG.parent
 _CSRC = _PKG / "csrc"
 _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
-SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_tblock3.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
+SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_tblock3.cu", "srj_sph.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -126,6 +126,13 @@ SIGNATURES = {
     "srj_batch_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I64, _VP,
                              ctypes.POINTER(Stats), _DP]),
     "srj_batch_last_error": (ctypes.c_char_p, []),
+    "srj_sph_coefficients": (_I, [_I, _I64P, _DP, _DP, _DP]),
+    "srj_sph_plan_create": (_I, [ctypes.POINTER(_VP), _I, _I64P, _DP, _DP, _DP, _I, _DP, _I32P, _I32P]),
+    "srj_sph_plan_destroy": (_I, [_VP]),
+    "srj_sph_steps": (_I, [_VP, _VP, _VP, _I64, _I64, _VP]),
+    "srj_sph_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),
+    "srj_sph_solve": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
+    "srj_sph_finalize": (_I, [_VP, _VP, _VP]),
     "srj_last_error": (ctypes.c_char_p, []),
     "srj_version": (ctypes.c_char_p, []),
 }

@@ -136,6 +136,11 @@ cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const BatchProb* probs
 std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin);
 double host_max_cycle_log10(const std::vector<double>& w, const std::vector<int32_t>& q, int nd, const int64_t* dims);
 double host_kappa_min(int nd, const int64_t* dims);
+// log10 of max |Gamma(kappa)| over [kmin, kmax] for the integer scheme (omega, q).
+double host_max_cycle_log10_range(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin,
+                                  double kmax);
+// Record the message returned by srj_last_error; returns code.
+int set_last_error(int code, const char* msg);
 
 // Set the ghost layer of a padded float64 grid to 0.
 cudaError_t launch_zero_ghosts(const Geom& g, double* a, cudaStream_t s);

@@ -223,6 +223,11 @@ double host_max_cycle_log10(const std::vector<double>& w, const std::vector<int3
     return kmin < kmax ? max_cycle_log10(w, q, kmin, kmax) : cycle_log10(w, q, kmin);
 }
 double host_kappa_min(int nd, const int64_t* dims) { return kappa_min_of(nd, dims); }
+double host_max_cycle_log10_range(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin,
+                                  double kmax) {
+    return max_cycle_log10(w, q, kmin, kmax);
+}
+int set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace srj
 
 struct srj_plan {

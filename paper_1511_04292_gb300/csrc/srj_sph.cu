@@ -1,0 +1,477 @@
+// SRJ on the spherical-coordinate operators of Sect. 5.2 (FP64).
+//
+// The Poisson equation in (r, theta[, phi]) multiplied by r^2, discretised by
+// second-order central differences on cell centres r_i = (i - 1/2) dr,
+// theta_j = (j - 1/2) dtheta, phi_k = (k - 1/2) dphi, has separable
+// coefficients:
+//   (L u)_p = cr_m[i] u(i-1) + cr_p[i] u(i+1) + ct_m[j] u(j-1) + ct_p[j] u(j+1)
+//             [+ cp[j] (u(k-1) + u(k+1))] - d_p u_p,
+//   d_p = cr_0[i] + ct_0[j] [+ (cp[j] + cp[j])],   L u = b = r^2 s.
+// Boundary prescriptions of Sect. 5.2, applied at every step: Dirichlet data in
+// the r = 1 ghost layer; u_0 = u_1 = u_2 at r = 0 (row i = 1 copies row 2, and
+// row 2 sees u(i-1) = u(i)); Neumann mirrors at theta = 0, pi; periodic phi.
+// The weighted-Jacobi step (Sect. 3.1 on this operator, diagonal -d):
+//   res = (s - d u_p) - b_p,   u'_p = u_p + omega (res / d),
+// each operation rounded once, in this order (the FP64 oracle's order, so the
+// two agree bit for bit).  The SRJ cycle is that of the Poisson plans (Sect. 2).
+#include "srj_internal.h"
+#include "../../include/srj.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace srj_sph {
+// Device pointers to the separable coefficients (padded index order).
+struct Coef {
+    const double* cr_m; const double* cr_p; const double* cr_0;
+    const double* ct_m; const double* ct_p; const double* ct_0;
+    const double* cp;
+};
+}  // namespace srj_sph
+
+namespace {
+
+using srj_sph::Coef;
+constexpr int kResBlocks = 304;   // residual partials (fixed: deterministic reduction order)
+constexpr int kResThreads = 256;
+
+// res and d at the active point (i, j, k) of u.
+template <int ND>
+__device__ __forceinline__ double sph_res(const srj::Geom& g, const Coef& c, const double* __restrict__ b,
+                                          const double* __restrict__ u, int i, int j, int k, int64_t p, double* d_out) {
+    const double cc = u[p];
+    const double um = (i == 2) ? cc : u[p - 1];
+    const double up = u[p + 1];
+    const double tm = (j == 1) ? cc : u[p - g.sx64];
+    const double tp = (j == g.ny) ? cc : u[p + g.sx64];
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(c.cr_m[i], um), __dmul_rn(c.cr_p[i], up)),
+                         __dadd_rn(__dmul_rn(c.ct_m[j], tm), __dmul_rn(c.ct_p[j], tp)));
+    double d = __dadd_rn(c.cr_0[i], c.ct_0[j]);
+    if (ND == 3) {
+        const double pm = (k == 1) ? u[p + (int64_t)(g.nz - 1) * g.sy64] : u[p - g.sy64];
+        const double pp = (k == g.nz) ? u[p - (int64_t)(g.nz - 1) * g.sy64] : u[p + g.sy64];
+        s = __dadd_rn(s, __dmul_rn(c.cp[j], __dadd_rn(pm, pp)));
+        d = __dadd_rn(d, __dadd_rn(c.cp[j], c.cp[j]));
+    }
+    *d_out = d;
+    return __dsub_rn(__dsub_rn(s, __dmul_rn(d, cc)), b[p]);
+}
+
+template <int ND>
+__global__ void k_sph_sweep(srj::Geom g, Coef c, double omega, const double* __restrict__ b,
+                            const double* __restrict__ uin, double* __restrict__ uout) {
+    const int i = 2 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (i > g.nx || j > g.ny) return;
+    const int k0 = ND == 3 ? 1 : 0, k1 = ND == 3 ? g.nz : 0;
+    for (int k = k0 + (int)blockIdx.z; k <= k1; k += (int)gridDim.z) {
+        const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        double d;
+        const double res = sph_res<ND>(g, c, b, uin, i, j, k, p, &d);
+        const double o = __dadd_rn(uin[p], __dmul_rn(omega, __ddiv_rn(res, d)));
+        uout[p] = o;
+        if (i == 2) uout[p - 1] = o;  // u_1 = u_2
+    }
+}
+
+// Per-block partial (sum of res^2, max |res|) over the active points; r (if given) gets res.
+template <int ND>
+__global__ void k_sph_residual(srj::Geom g, Coef c, const double* __restrict__ b, const double* __restrict__ u,
+                               double* __restrict__ r, double* __restrict__ partials) {
+    const int64_t na = (int64_t)(g.nx - 1) * g.ny;  // active points per plane
+    const int64_t nk = ND == 3 ? g.nz : 1;
+    double ss = 0.0, mx = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < na * nk; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kk = t / na, rem = t % na;
+        const int j = 1 + (int)(rem / (g.nx - 1));
+        const int i = 2 + (int)(rem % (g.nx - 1));
+        const int k = ND == 3 ? 1 + (int)kk : 0;
+        const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        double d;
+        const double res = sph_res<ND>(g, c, b, u, i, j, k, p, &d);
+        if (r) r[p] = res;
+        ss = __dadd_rn(ss, __dmul_rn(res, res));
+        mx = fmax(mx, fabs(res));
+    }
+    __shared__ double s_ss[kResThreads / 32], s_mx[kResThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ss = __dadd_rn(ss, __shfl_down_sync(0xffffffffu, ss, o));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { s_ss[w] = ss; s_mx[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = 0.0;
+        for (int q = 0; q < kResThreads / 32; ++q) { a = __dadd_rn(a, s_ss[q]); m = fmax(m, s_mx[q]); }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = m;
+    }
+}
+
+__global__ void k_sph_norms(const double* __restrict__ partials, int n, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, m = 0.0;
+    for (int q = 0; q < n; ++q) { a = __dadd_rn(a, partials[2 * q]); m = fmax(m, partials[2 * q + 1]); }
+    out[0] = sqrt(a);
+    out[1] = m;
+}
+
+// Ghost layer and row i = 1 from the prescriptions (the r = 1 ghost is data).
+__global__ void k_sph_fin_r(srj::Geom g, double* __restrict__ u) {  // (j, k): u_1 = u_2, u_0 = u_1
+    const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int k = (g.nd == 3 ? 1 : 0) + (int)blockIdx.y;
+    if (j > g.ny) return;
+    const int64_t q = (g.nd == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64;
+    if (g.nx >= 2) u[q + 1] = u[q + 2];
+    u[q] = u[q + 1];
+}
+__global__ void k_sph_fin_t(srj::Geom g, double* __restrict__ u) {  // (i, k): theta mirrors
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int k = (g.nd == 3 ? 1 : 0) + (int)blockIdx.y;
+    if (i > g.nx + 1) return;
+    const int64_t base = (g.nd == 3 ? (int64_t)k * g.sy64 : 0);
+    u[base + i] = u[base + g.sx64 + i];
+    u[base + (int64_t)(g.ny + 1) * g.sx64 + i] = u[base + (int64_t)g.ny * g.sx64 + i];
+}
+__global__ void k_sph_fin_p(srj::Geom g, double* __restrict__ u) {  // (i, j): periodic phi
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= g.sy64) return;
+    u[t] = u[(int64_t)g.nz * g.sy64 + t];
+    u[(int64_t)(g.nz + 1) * g.sy64 + t] = u[g.sy64 + t];
+}
+
+}  // namespace
+
+struct srj_sph_plan {
+    int device = 0;
+    int nd = 2;
+    srj::Geom g{};
+    double* coef = nullptr;  // device: radial (3 (nx+2)) | polar (3 (ny+2)) | azim (ny+2)
+    srj_sph::Coef c{};
+    std::vector<double> seq;  // ordered weights of one M-cycle
+    double* ua = nullptr;
+    double* ub = nullptr;
+    double* bb = nullptr;
+    double* partials = nullptr;
+    double* norms = nullptr;
+    double* host_norms = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t cycle = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int sfail(int code, const char* msg) { return srj::set_last_error(code, msg); }
+
+#define SPH_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return sfail(SRJ_ERR_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+cudaError_t launch_sweep(const srj_sph_plan* p, double omega, const double* b, const double* uin, double* uout,
+                         cudaStream_t s) {
+    if (p->g.nx < 2) return cudaSuccess;  // no active point
+    dim3 blk(128, 2, 1);
+    dim3 grd((unsigned)((p->g.nx - 1 + 127) / 128), (unsigned)((p->g.ny + 1) / 2),
+             p->nd == 3 ? (unsigned)std::min(p->g.nz, 64) : 1u);
+    if (p->nd == 3) k_sph_sweep<3><<<grd, blk, 0, s>>>(p->g, p->c, omega, b, uin, uout);
+    else            k_sph_sweep<2><<<grd, blk, 0, s>>>(p->g, p->c, omega, b, uin, uout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const srj_sph_plan* p, const double* b, const double* u, double* r, cudaStream_t s) {
+    if (p->g.nx < 2) {
+        cudaError_t e = cudaMemsetAsync(p->norms, 0, 2 * sizeof(double), s);
+        return e;
+    }
+    if (p->nd == 3) k_sph_residual<3><<<kResBlocks, kResThreads, 0, s>>>(p->g, p->c, b, u, r, p->partials);
+    else            k_sph_residual<2><<<kResBlocks, kResThreads, 0, s>>>(p->g, p->c, b, u, r, p->partials);
+    k_sph_norms<<<1, 32, 0, s>>>(p->partials, kResBlocks, p->norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const srj_sph_plan* p, double* u, cudaStream_t s) {
+    const unsigned nk = p->nd == 3 ? (unsigned)p->g.nz : 1u;
+    k_sph_fin_r<<<dim3((unsigned)((p->g.ny + 127) / 128), nk), 128, 0, s>>>(p->g, u);
+    k_sph_fin_t<<<dim3((unsigned)((p->g.nx + 2 + 127) / 128), nk), 128, 0, s>>>(p->g, u);
+    if (p->nd == 3) k_sph_fin_p<<<(unsigned)((p->g.sy64 + 255) / 256), 256, 0, s>>>(p->g, u);
+    return cudaGetLastError();
+}
+
+int read_norms(srj_sph_plan* p, cudaStream_t s, double* l2, double* linf) {
+    SPH_CUDA(cudaMemcpyAsync(p->host_norms, p->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    *l2 = p->host_norms[0];
+    *linf = p->host_norms[1];
+    return SRJ_OK;
+}
+
+int check_plan(srj_sph_plan* p) {
+    if (!p) return sfail(SRJ_ERR_INVALID_ARG, "plan is NULL");
+    int dev = -1;
+    SPH_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return sfail(SRJ_ERR_INVALID_ARG, "plan was created on another device");
+    return SRJ_OK;
+}
+
+void destroy(srj_sph_plan* p) {
+    if (!p) return;
+    if (p->cycle) cudaGraphExecDestroy(p->cycle);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    cudaFree(p->coef); cudaFree(p->ua); cudaFree(p->ub); cudaFree(p->bb); cudaFree(p->partials);
+    cudaFree(p->norms);
+    if (p->host_norms) cudaFreeHost(p->host_norms);
+    delete p;
+}
+
+// One M-cycle from ua back into ua (an odd M ends with a copy).
+int capture_cycle(srj_sph_plan* p) {
+    cudaGraph_t graph = nullptr;
+    SPH_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    const size_t bytes = sizeof(double) * (size_t)p->g.n64;
+    for (size_t k = 0; k < p->seq.size() && err == cudaSuccess; ++k) {
+        const bool from_a = (k % 2) == 0;
+        err = launch_sweep(p, p->seq[k], p->bb, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->cap);
+    }
+    if (err == cudaSuccess && (p->seq.size() % 2) == 1)
+        err = cudaMemcpyAsync(p->ua, p->ub, bytes, cudaMemcpyDeviceToDevice, p->cap);
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SPH_CUDA(err); }
+    SPH_CUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&p->cycle, graph, 0);
+    cudaGraphDestroy(graph);
+    SPH_CUDA(e3);
+    return SRJ_OK;
+}
+
+int load_inputs(srj_sph_plan* p, const double* b, const double* u, cudaStream_t s) {
+    const size_t bytes = sizeof(double) * (size_t)p->g.n64;
+    SPH_CUDA(cudaMemcpyAsync(p->bb, b, bytes, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(cudaMemcpyAsync(p->ua, u, bytes, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(cudaMemcpyAsync(p->ub, u, bytes, cudaMemcpyDeviceToDevice, s));
+    return SRJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srj_sph_coefficients(int ndim, const int64_t* dims, double* radial, double* polar, double* azim) {
+    if ((ndim != 2 && ndim != 3) || !dims || !radial || !polar || (ndim == 3 && !azim))
+        return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < ndim; ++i)
+        if (dims[i] < 1 || dims[i] > (int64_t)1 << 20) return sfail(SRJ_ERR_INVALID_ARG, "dims must be in 1..2^20");
+    const double pi = 3.14159265358979323846;
+    const int64_t nr = dims[0], nt = dims[1];
+    const double dr = 1.0 / (double)nr, dt = pi / (double)nt;
+    for (int64_t i = 0; i < nr + 2; ++i) {
+        const double r = ((double)i - 0.5) * dr;
+        radial[i] = r * (r - dr) / (dr * dr);
+        radial[(nr + 2) + i] = r * (r + dr) / (dr * dr);
+        radial[2 * (nr + 2) + i] = 2.0 * r * r / (dr * dr);
+    }
+    for (int64_t j = 0; j < nt + 2; ++j) {
+        polar[j] = polar[(nt + 2) + j] = polar[2 * (nt + 2) + j] = 0.0;
+        if (ndim == 3) azim[j] = 0.0;
+        if (j < 1 || j > nt) continue;
+        const double t = ((double)j - 0.5) * dt;
+        const double cot = std::cos(t) / std::sin(t);
+        polar[j] = 1.0 / (dt * dt) - cot / (2.0 * dt);
+        polar[(nt + 2) + j] = 1.0 / (dt * dt) + cot / (2.0 * dt);
+        polar[2 * (nt + 2) + j] = 2.0 / (dt * dt);
+        if (ndim == 3) {
+            const double dp = 2.0 * pi / (double)dims[2];
+            const double sn = std::sin(t);
+            azim[j] = 1.0 / (sn * sn * dp * dp);
+        }
+    }
+    return SRJ_OK;
+}
+
+int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, const double* radial,
+                        const double* polar, const double* azim, int P, const double* omega, const int32_t* q,
+                        const int32_t* order) {
+    if (!out) return sfail(SRJ_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if ((ndim != 2 && ndim != 3) || !dims || !radial || !polar || (ndim == 3 && !azim) || !omega || !q)
+        return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    if (P < 1 || P > 32) return sfail(SRJ_ERR_INVALID_ARG, "P must be in 1..32");
+    for (int i = 0; i < ndim; ++i)
+        if (dims[i] < 1 || dims[i] > 65536) return sfail(SRJ_ERR_INVALID_ARG, "dims must be in 1..65536");
+    std::vector<double> w(omega, omega + P);
+    std::vector<int32_t> qq(q, q + P);
+    int64_t M = 0;
+    for (int i = 0; i < P; ++i) {
+        if (!(std::isfinite(w[i]) && w[i] > 0.0)) return sfail(SRJ_ERR_INVALID_ARG, "weights must be finite and > 0");
+        if (qq[i] < 1) return sfail(SRJ_ERR_INVALID_ARG, "repetitions must be >= 1");
+        M += qq[i];
+    }
+    if (M > ((int64_t)1 << 20)) return sfail(SRJ_ERR_INVALID_ARG, "M must be <= 2^20");
+    // Contraction of the integer scheme on [1 / max omega, 2): all roots of the
+    // cycle polynomial lie in [1 / max omega, 2), below it the polynomial falls
+    // monotonically from 1, and the Jacobi-scaled operator has its spectrum in
+    // (0, 2): rows weakly diagonally dominant with the boundary prescriptions,
+    // strictly in the rows next to the Dirichlet boundary, and irreducible.
+    const double wmax = *std::max_element(w.begin(), w.end());
+    const double kmax = 2.0 * (1.0 - 1e-12);
+    if (!(srj::host_max_cycle_log10_range(w, qq, std::min(1.0 / wmax, 0.5 * kmax), kmax) < 0.0))
+        return sfail(SRJ_ERR_BAD_SCHEDULE, "the integer scheme does not contract on [1/omega_max, 2)");
+    std::vector<int32_t> ord;
+    if (order) {
+        ord.assign(order, order + M);
+        std::vector<int64_t> cnt(P, 0);
+        for (int32_t v : ord) {
+            if (v < 0 || v >= P) return sfail(SRJ_ERR_INVALID_ARG, "order entries must be in 0..P-1");
+            ++cnt[v];
+        }
+        for (int i = 0; i < P; ++i)
+            if (cnt[i] != qq[i]) return sfail(SRJ_ERR_INVALID_ARG, "order must hold level i exactly q_i times");
+    } else {
+        ord = srj::host_drift_order(w, qq, 1.0 / wmax);
+    }
+    auto* p = new srj_sph_plan();
+    p->nd = ndim;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return sfail(SRJ_ERR_CUDA, "no device"); }
+    p->g = srj::make_geom(ndim, dims);
+    p->seq.resize((size_t)M);
+    for (int64_t k = 0; k < M; ++k) p->seq[(size_t)k] = w[(size_t)ord[(size_t)k]];
+    const int64_t nr = dims[0], nt = dims[1];
+    const size_t ncoef = (size_t)(3 * (nr + 2) + 3 * (nt + 2) + (nt + 2));
+    std::vector<double> hc(ncoef, 0.0);
+    std::copy(radial, radial + 3 * (nr + 2), hc.begin());
+    std::copy(polar, polar + 3 * (nt + 2), hc.begin() + 3 * (nr + 2));
+    if (ndim == 3) std::copy(azim, azim + (nt + 2), hc.begin() + 3 * (nr + 2) + 3 * (nt + 2));
+    for (double v : hc)
+        if (!std::isfinite(v)) { delete p; return sfail(SRJ_ERR_INVALID_ARG, "coefficients must be finite"); }
+    const size_t bytes = sizeof(double) * (size_t)p->g.n64;
+    if (cudaMalloc(&p->coef, sizeof(double) * ncoef) != cudaSuccess || cudaMalloc(&p->ua, bytes) != cudaSuccess ||
+        cudaMalloc(&p->ub, bytes) != cudaSuccess || cudaMalloc(&p->bb, bytes) != cudaSuccess ||
+        cudaMalloc(&p->partials, sizeof(double) * 2 * kResBlocks) != cudaSuccess ||
+        cudaMalloc(&p->norms, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->host_norms, 2 * sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess ||
+        cudaMemcpy(p->coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        destroy(p);
+        return sfail(SRJ_ERR_CUDA, "plan allocation failed");
+    }
+    const double* base = p->coef;
+    p->c = Coef{base, base + (nr + 2), base + 2 * (nr + 2), base + 3 * (nr + 2), base + 3 * (nr + 2) + (nt + 2),
+                base + 3 * (nr + 2) + 2 * (nt + 2), base + 3 * (nr + 2) + 3 * (nt + 2)};
+    int rc = capture_cycle(p);
+    if (rc != SRJ_OK) { destroy(p); return rc; }
+    *out = p;
+    return SRJ_OK;
+}
+
+int srj_sph_plan_destroy(srj_sph_plan_t plan) {
+    if (!plan) return SRJ_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    const int pdev = plan->device;
+    if (dev != pdev) cudaSetDevice(pdev);
+    cudaStreamSynchronize(plan->cap);
+    destroy(plan);
+    if (dev >= 0 && dev != pdev) cudaSetDevice(dev);
+    return SRJ_OK;
+}
+
+int srj_sph_steps(srj_sph_plan_t p, const double* b, double* u, int64_t first, int64_t count, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!b || !u || first < 0 || count < 0) return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = load_inputs(p, b, u, s);
+    if (rc) return rc;
+    const int64_t M = (int64_t)p->seq.size();
+    double *in = p->ua, *out = p->ub;
+    for (int64_t k = 0; k < count; ++k) {
+        SPH_CUDA(launch_sweep(p, p->seq[(size_t)((first + k) % M)], p->bb, in, out, s));
+        std::swap(in, out);
+    }
+    SPH_CUDA(cudaMemcpyAsync(u, in, sizeof(double) * (size_t)p->g.n64, cudaMemcpyDeviceToDevice, s));
+    return SRJ_OK;
+}
+
+int srj_sph_residual(srj_sph_plan_t p, const double* b, const double* u, double* r_out, double* l2, double* linf,
+                     void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!b || !u || !l2 || !linf) return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r_out) SPH_CUDA(cudaMemsetAsync(r_out, 0, sizeof(double) * (size_t)p->g.n64, s));
+    SPH_CUDA(launch_residual(p, b, u, r_out, s));
+    return read_norms(p, s, l2, linf);
+}
+
+int srj_sph_solve(srj_sph_plan_t p, const double* b, double* u, double tol, int64_t max_cycles, void* stream,
+                  srj_stats_t* stats) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!b || !u || !(tol >= 0.0) || max_cycles < 0) return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    srj_stats_t st{};
+    rc = load_inputs(p, b, u, s);
+    if (rc) return rc;
+    double l2 = 0.0, linf = 0.0;
+    SPH_CUDA(launch_residual(p, p->bb, p->ua, nullptr, s));
+    rc = read_norms(p, s, &l2, &linf);
+    if (rc) return rc;
+    st.residual_checks = 1;
+    st.r0_l2 = l2;
+    int status = SRJ_ERR_NOT_CONVERGED;
+    if (l2 == 0.0) status = SRJ_OK;
+    else if (!std::isfinite(l2)) status = SRJ_ERR_DIVERGED;
+    double best = l2;
+    int stall = 0;
+    float ms_total = 0.f;
+    for (int64_t c = 1; status == SRJ_ERR_NOT_CONVERGED && c <= max_cycles; ++c) {
+        SPH_CUDA(cudaEventRecord(p->ev0, s));
+        SPH_CUDA(cudaGraphLaunch(p->cycle, s));
+        SPH_CUDA(cudaEventRecord(p->ev1, s));
+        SPH_CUDA(launch_residual(p, p->bb, p->ua, nullptr, s));
+        rc = read_norms(p, s, &l2, &linf);
+        if (rc) return rc;
+        float ms = 0.f;
+        SPH_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        ms_total += ms;
+        st.cycles = c;
+        st.sweeps = c * (int64_t)p->seq.size();
+        st.residual_checks += 1;
+        if (!std::isfinite(l2) || l2 > 1e6 * st.r0_l2) { status = SRJ_ERR_DIVERGED; break; }
+        if (l2 <= tol * st.r0_l2) { status = SRJ_OK; break; }
+        // floating-point floor: the residual has not halved its best value for 4 cycles
+        if (l2 < 0.5 * best) { best = l2; stall = 0; }
+        else if (++stall >= 4) { st.stagnated = 1; break; }
+    }
+    SPH_CUDA(launch_finalize(p, p->ua, s));
+    SPH_CUDA(cudaMemcpyAsync(u, p->ua, sizeof(double) * (size_t)p->g.n64, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(cudaStreamSynchronize(s));
+    st.res_l2 = l2;
+    st.res_linf = linf;
+    st.rel_res = st.r0_l2 > 0.0 ? l2 / st.r0_l2 : 0.0;
+    st.sweep_ms = ms_total;
+    if (stats) *stats = st;
+    if (status == SRJ_ERR_NOT_CONVERGED) return sfail(status, "tolerance not reached");
+    if (status == SRJ_ERR_DIVERGED) return sfail(status, "residual diverged");
+    return SRJ_OK;
+}
+
+int srj_sph_finalize(srj_sph_plan_t p, double* u, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!u) return sfail(SRJ_ERR_INVALID_ARG, "u is NULL");
+    SPH_CUDA(launch_finalize(p, u, (cudaStream_t)stream));
+    return SRJ_OK;
+}
+
+}  // extern "C"

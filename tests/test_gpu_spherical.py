@@ -1,0 +1,108 @@
+"""Parity of the spherical-operator path (Sect. 5.2, FP64) with the oracle:
+sweeps and residual fields bit for bit, solves cycle for cycle, and the paper's
+analytic test at the oracle's discretisation error."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
+import paper_1511_04292_gb300.schedules as sch  # noqa: E402
+from paper_1511_04292_gb300 import spherical as sp  # noqa: E402
+
+from test_oracle_spherical import paper_problem_2d  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(37, 23), (2, 2), (1, 4), (130, 67), (5, 300), (13, 11, 9), (2, 3, 1), (32, 5, 7), (3, 8, 2)]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def schedule(P=5):
+    row = sch.lookup(2, 64, P)
+    return row["omega"], row["q"], row["order"]
+
+
+def problem(dims, seed):
+    rng = np.random.default_rng(seed)
+    shape = oracle.padded_shape(dims)
+    return rng.standard_normal(shape), rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_sweeps_bit_identical(dims):
+    omega, q, order = schedule(5)
+    coef = sp.coefficients(dims)
+    plan = sp.SphericalPlan(dims, omega, q, order, coef=coef)
+    b, u = problem(dims, 3)
+    seq = oracle.omega_sequence(omega, order)
+    ref = u.copy()
+    for k in range(7):
+        ref = oracle.sph_sweep(dims, coef, seq[(2 + k) % len(seq)], b, ref)
+    ud = dev(u)
+    plan.steps(dev(b), ud, 2, 7)
+    assert np.array_equal(ud.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_residual_field_bit_identical(dims):
+    omega, q, order = schedule(5)
+    coef = sp.coefficients(dims)
+    plan = sp.SphericalPlan(dims, omega, q, order, coef=coef)
+    b, u = problem(dims, 5)
+    l2, linf, r = oracle.sph_residual(dims, coef, b, u, want_r=True)
+    rd = torch.empty_like(dev(u))
+    gl2, glinf = plan.residual(dev(b), dev(u), rd)
+    assert np.array_equal(rd.cpu().numpy(), r)
+    assert glinf == linf
+    assert gl2 == pytest.approx(l2, rel=1e-12, abs=1e-300)
+
+
+@pytest.mark.parametrize("dims", [(40, 30), (12, 10, 8), (1, 3)])
+def test_solve_matches_oracle_cycle_for_cycle(dims):
+    omega, q, order = schedule(6)
+    coef = sp.coefficients(dims)
+    plan = sp.SphericalPlan(dims, omega, q, order, coef=coef)
+    b, u0 = problem(dims, 7)
+    seq = oracle.omega_sequence(omega, order)
+    ref = u0.copy()
+    so = oracle.sph_solve(dims, coef, seq, b, ref, 1e-10, 500)
+    ud = dev(u0)
+    st = plan.solve(dev(b), ud, 1e-10, 500)
+    assert so["status"] == oracle.CONVERGED and st["cycles"] == so["cycles"]
+    assert np.array_equal(ud.cpu().numpy(), ref)
+    assert st["rel_res"] == pytest.approx(so["rel"], rel=1e-10, abs=1e-300)
+
+
+def test_paper_problem_reaches_the_discretisation_error():
+    """Sect. 5.2 axisymmetric test (l = 0, 2 terms), N = 256: the GPU solve
+    reaches the oracle's discretisation error (second order: 1.5e-5)."""
+    N = 256
+    dims = (N, N)
+    ua, b = paper_problem_2d(N, N)
+    u0 = np.zeros_like(ua)
+    u0[:, -1] = ua[:, -1]
+    row = sch.lookup(2, 256, 8)
+    plan = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"])
+    ud = dev(u0)
+    st = plan.solve(dev(b), ud, 1e-12, 2000)
+    u = ud.cpu().numpy()
+    err = np.abs(u - ua)[1:-1, 2:-1].max()
+    assert 1.0e-5 < err < 2.5e-5, (err, st)
+    # prescriptions hold on the returned field
+    assert np.array_equal(u[1:-1, 1], u[1:-1, 2]) and np.array_equal(u[1:-1, 0], u[1:-1, 2])
+    assert np.array_equal(u[0], u[1]) and np.array_equal(u[-1], u[-2])
+
+
+def test_bad_schedule_and_bad_arguments_are_rejected():
+    with pytest.raises(Exception):
+        sp.SphericalPlan((8, 8), [3.0], [1])  # 1 - 3 kappa reaches -5 at kappa = 2: no contraction
+    with pytest.raises(Exception):
+        sp.SphericalPlan((0, 8), [1.0], [1])
+    plan = sp.SphericalPlan((8, 8), [1.0], [1])
+    with pytest.raises(Exception):
+        plan.solve(dev(np.zeros((10, 10))), dev(np.zeros((9, 10))), 1e-8, 10)
