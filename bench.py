@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 3-D 512^3 and batched secondary measurements")
-    ap.add_argument("--kernel-case", choices=["f32", "f64"], default=None,
+    ap.add_argument("--kernel-case", choices=["f32", "f64", "sph"], default=None,
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
@@ -74,6 +74,15 @@ def run_kernel_case(args):
     n = args.n
     torch.cuda.set_device(0)
     dims = (n,) * args.ndim
+    if args.kernel_case == "sph":
+        from paper_1511_04292_gb300 import spherical as sp
+        splan = sp.SphericalPlan(dims, [1.0], [1])
+        f = torch.from_numpy(W.random_field(dims, 1)).cuda()
+        u = torch.from_numpy(W.random_field(dims, 2)).cuda()
+        splan.steps(f, u, 0, args.count)
+        torch.cuda.synchronize()
+        print("kernel case sph n=%d^%d count=%d done" % (n, args.ndim, args.count))
+        return 0
     plan = srj.Plan(dims, 1.0 / (n + 1), [1.0], [1], None, "mixed" if args.kernel_case == "f32" else "fp64")
     if args.T is not None:
         plan.set_temporal_depth(args.T)
@@ -186,6 +195,24 @@ def secondary_workloads(stream):
         "sweep_kernel": "k_sweep3_f32_tb2 (2 steps per launch)" if plan.temporal_depth() == 2 else "k_sweep_f32<3>",
         "effective_gbs_per_step": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
     del f, u0, u, plan
+    torch.cuda.empty_cache()
+    # spherical (Sect. 5.2 operator, axisymmetric r-theta), 1024^2, FP64, P = 10, tol 1e-10
+    from paper_1511_04292_gb300 import spherical as sp
+    ns = 1024
+    b_h, u0_h = W.spherical_problem_2d(ns, 5)
+    bs = torch.from_numpy(b_h).cuda(); us0 = torch.from_numpy(u0_h).cuda(); us = torch.empty_like(us0)
+    row = srj.schedules.lookup(2, ns, 10)
+    splan = sp.SphericalPlan((ns, ns), row["omega"], row["q"], row["order"])
+    us.copy_(us0); splan.solve(bs, us, 1e-10, 400)  # warm-up
+    us.copy_(us0); torch.cuda.synchronize()
+    a.record(stream); st = splan.solve(bs, us, 1e-10, 400); b.record(stream); torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    act = (ns - 1) * ns
+    out["spherical_2d_1024x1024_P10_fp64_tol1e-10"] = {
+        "time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * act / (ms / 1e3) / 1e9, "cycles": st["cycles"],
+        "final_rel_residual": st["rel_res"], "sweep_kernel": "k_sph_sweep<2> (FP64)",
+        "sweep_kernel_gbs": 24.0 * act * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
+    del bs, us0, us, splan
     torch.cuda.empty_cache()
     # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10
     specs = W.batch_specs()

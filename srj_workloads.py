@@ -151,6 +151,40 @@ def random_field(dims, seed, scale=1.0):
 
 
 # ---------------------------------------------------------------------------
+# Spherical test of Sect. 5.2 (axisymmetric r-theta grid)
+# ---------------------------------------------------------------------------
+
+def spherical_problem_2d(n, seed, realistic=False):
+    """(b, u0) of the Sect. 5.2 test on an n x n (r, theta) cell-centred grid,
+    truncated to the l = 0 and l = 2 terms of Eqs. grav:source / grav:sol
+    (a_l = 2^-l, k_l the first root of j_l, b_l = c_l from continuity at r = 1).
+    b = r^2 s; u0: the analytic solution in the r = 1 ghost layer, zero inside
+    (ab initio), or u_analytic (1 + U(-1/2, 1/2) / n) inside (realistic start,
+    seeded).  Layout (n + 2, n + 2): theta slowest, r fastest."""
+    from scipy.optimize import brentq
+    from scipy.special import spherical_jn as jn
+    dr, dt = 1.0 / n, math.pi / n
+    r = (np.arange(n + 2) - 0.5) * dr
+    t = (np.arange(n + 2) - 0.5) * dt
+    R, Th = np.meshgrid(r, t)
+    P2 = 0.5 * (3 * np.cos(Th) ** 2 - 1)
+    k0, k2 = math.pi, brentq(lambda x: jn(2, x), 5.0, 6.5)
+    a0, a2 = 1.0, 0.25
+    b0 = a0 * k0 * jn(1, k0)
+    b2 = -a2 / 5 * (2 * jn(2, k2) - k2 * jn(3, k2))
+    Rin = np.where(R <= 1, R, 1.0)
+    ua = np.where(R <= 1, (a0 * jn(0, k0 * Rin) + b0) + (a2 * jn(2, k2 * Rin) + b2 * Rin ** 2) * P2,
+                  b0 / R + b2 / R ** 3 * P2)
+    s = np.where(R <= 1, -a0 * k0 ** 2 * jn(0, k0 * Rin) - a2 * k2 ** 2 * jn(2, k2 * Rin) * P2, 0.0)
+    u0 = np.zeros_like(ua)
+    if realistic:
+        rng = np.random.default_rng(seed)
+        u0 = ua * (1.0 + rng.uniform(-0.5, 0.5, ua.shape) / n)
+    u0[:, -1] = ua[:, -1]
+    return np.ascontiguousarray(R ** 2 * s), np.ascontiguousarray(u0)
+
+
+# ---------------------------------------------------------------------------
 # Workload 4: the batch of independent 2-D problems
 # ---------------------------------------------------------------------------
 
