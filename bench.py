@@ -196,23 +196,29 @@ def secondary_workloads(stream):
         "effective_gbs_per_step": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
     del f, u0, u, plan
     torch.cuda.empty_cache()
-    # spherical (Sect. 5.2 operator, axisymmetric r-theta), 1024^2, FP64, P = 10, tol 1e-10
+    # spherical (Sect. 5.2 operator, axisymmetric r-theta), 1024^2, P = 10, tol 1e-10: mixed, and FP64 beside it
     from paper_1511_04292_gb300 import spherical as sp
     ns = 1024
     b_h, u0_h = W.spherical_problem_2d(ns, 5)
     bs = torch.from_numpy(b_h).cuda(); us0 = torch.from_numpy(u0_h).cuda(); us = torch.empty_like(us0)
     row = srj.schedules.lookup(2, ns, 10)
-    splan = sp.SphericalPlan((ns, ns), row["omega"], row["q"], row["order"])
-    us.copy_(us0); splan.solve(bs, us, 1e-10, 400)  # warm-up
-    us.copy_(us0); torch.cuda.synchronize()
-    a.record(stream); st = splan.solve(bs, us, 1e-10, 400); b.record(stream); torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
     act = (ns - 1) * ns
-    out["spherical_2d_1024x1024_P10_fp64_tol1e-10"] = {
-        "time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * act / (ms / 1e3) / 1e9, "cycles": st["cycles"],
-        "final_rel_residual": st["rel_res"], "sweep_kernel": "k_sph_sweep<2> (FP64)",
-        "sweep_kernel_gbs": 24.0 * act * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
-    del bs, us0, us, splan
+    res = {}
+    for prec in ("mixed", "fp64"):
+        splan = sp.SphericalPlan((ns, ns), row["omega"], row["q"], row["order"], precision=prec)
+        us.copy_(us0); splan.solve(bs, us, 1e-10, 400)  # warm-up
+        us.copy_(us0); torch.cuda.synchronize()
+        a.record(stream); st = splan.solve(bs, us, 1e-10, 400); b.record(stream); torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res[prec] = dict(time_to_tol_s=ms / 1e3, gupdates_per_s=st["sweeps"] * act / (ms / 1e3) / 1e9,
+                         cycles=st["cycles"], final_rel_residual=st["rel_res"],
+                         sweep_gbs=(12.0 if prec == "mixed" else 24.0) * act * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9)
+        del splan
+    out["spherical_2d_1024x1024_P10_mixed_tol1e-10"] = dict(
+        res["mixed"], sweep_kernel="k_sph_sweep_f32<2> (FP32 cycles, FP64 correction)",
+        fp64_comparator=dict(res["fp64"], sweep_kernel="k_sph_sweep<2> (FP64)"),
+        speedup_vs_fp64_time_to_tol=res["fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"])
+    del bs, us0, us
     torch.cuda.empty_cache()
     # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10
     specs = W.batch_specs()

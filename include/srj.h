@@ -397,18 +397,23 @@ typedef struct srj_sph_plan *srj_sph_plan_t;
 int srj_sph_coefficients(int ndim, const int64_t *dims, double *radial, double *polar, double *azim);
 
 /* Build a plan: dims and coefficient arrays (host, copied; finite); the
- * schedule as in srj_plan_create (order NULL: drift order).  The integer scheme
+ * schedule as in srj_plan_create (order NULL: drift order); precision
+ * SRJ_PREC_FP64 (every step in FP64) or SRJ_PREC_MIXED (each cycle runs in FP32
+ * on the defect equation L e = b - L u with e = 0 at the start and on the
+ * boundary, FP64 residual and update: the same cycle map up to FP32 rounding
+ * of the correction).  The integer scheme
  * must contract on [1 / max omega, 2) (SRJ_ERR_BAD_SCHEDULE); the Jacobi-scaled
  * operator's spectrum lies in (0, 2) for weakly diagonally dominant, irreducible
  * rows with strict dominance next to the Dirichlet boundary, which the Sect. 5.2
  * coefficients give. */
 int srj_sph_plan_create(srj_sph_plan_t *plan, int ndim, const int64_t *dims, const double *radial,
                         const double *polar, const double *azim, int P, const double *omega, const int32_t *q,
-                        const int32_t *order);
+                        const int32_t *order, int precision);
 int srj_sph_plan_destroy(srj_sph_plan_t plan);
 
-/* count steps of the cycle order from position first: u (device, in place);
- * writes the active points and row i = 1, leaves the other ghosts as given. */
+/* count FP64 steps of the cycle order from position first (either precision):
+ * u (device, in place); writes the active points and row i = 1, leaves the
+ * other ghosts as given. */
 int srj_sph_steps(srj_sph_plan_t plan, const double *b, double *u, int64_t first, int64_t count, void *stream);
 
 /* l2 / linf (host outputs) of res = L u - b over the active points; r_out

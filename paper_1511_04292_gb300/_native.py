@@ -127,7 +127,7 @@ SIGNATURES = {
                              ctypes.POINTER(Stats), _DP]),
     "srj_batch_last_error": (ctypes.c_char_p, []),
     "srj_sph_coefficients": (_I, [_I, _I64P, _DP, _DP, _DP]),
-    "srj_sph_plan_create": (_I, [ctypes.POINTER(_VP), _I, _I64P, _DP, _DP, _DP, _I, _DP, _I32P, _I32P]),
+    "srj_sph_plan_create": (_I, [ctypes.POINTER(_VP), _I, _I64P, _DP, _DP, _DP, _I, _DP, _I32P, _I32P, _I]),
     "srj_sph_plan_destroy": (_I, [_VP]),
     "srj_sph_steps": (_I, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "srj_sph_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),

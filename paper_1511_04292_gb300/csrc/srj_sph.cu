@@ -1,4 +1,5 @@
-// SRJ on the spherical-coordinate operators of Sect. 5.2 (FP64).
+// SRJ on the spherical-coordinate operators of Sect. 5.2: FP64, or mixed
+// precision (FP32 cycles on the defect equation inside FP64 defect correction).
 //
 // The Poisson equation in (r, theta[, phi]) multiplied by r^2, discretised by
 // second-order central differences on cell centres r_i = (i - 1/2) dr,
@@ -28,11 +29,17 @@ struct Coef {
     const double* ct_m; const double* ct_p; const double* ct_0;
     const double* cp;
 };
+struct Coef32 {
+    const float* cr_m; const float* cr_p; const float* cr_0;
+    const float* ct_m; const float* ct_p; const float* ct_0;
+    const float* cp;
+};
 }  // namespace srj_sph
 
 namespace {
 
 using srj_sph::Coef;
+using srj_sph::Coef32;
 constexpr int kResBlocks = 304;   // residual partials (fixed: deterministic reduction order)
 constexpr int kResThreads = 256;
 
@@ -119,6 +126,68 @@ __global__ void k_sph_norms(const double* __restrict__ partials, int n, double* 
     out[1] = m;
 }
 
+// FP32 step on the defect equation L e = r (mixed precision): the same stencil
+// and prescriptions; e has homogeneous Dirichlet data at r = 1.
+template <int ND>
+__global__ void k_sph_sweep_f32(srj::Geom g, Coef32 c, float omega, const float* __restrict__ r,
+                                const float* __restrict__ ein, float* __restrict__ eout) {
+    const int i = 2 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (i > g.nx || j > g.ny) return;
+    const int k0 = ND == 3 ? 1 : 0, k1 = ND == 3 ? g.nz : 0;
+    const float crm = c.cr_m[i], crp = c.cr_p[i], ctm = c.ct_m[j], ctp = c.ct_p[j];
+    float d = c.cr_0[i] + c.ct_0[j];
+    if (ND == 3) d += 2.0f * c.cp[j];
+    const float wd = omega / d;
+    for (int k = k0 + (int)blockIdx.z; k <= k1; k += (int)gridDim.z) {
+        const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        const float cc = ein[p];
+        const float um = (i == 2) ? cc : ein[p - 1];
+        const float up = ein[p + 1];
+        const float tm = (j == 1) ? cc : ein[p - g.sx64];
+        const float tp = (j == g.ny) ? cc : ein[p + g.sx64];
+        float s = (crm * um + crp * up) + (ctm * tm + ctp * tp);
+        if (ND == 3) {
+            const float pm = (k == 1) ? ein[p + (int64_t)(g.nz - 1) * g.sy64] : ein[p - g.sy64];
+            const float pp = (k == g.nz) ? ein[p - (int64_t)(g.nz - 1) * g.sy64] : ein[p + g.sy64];
+            s += c.cp[j] * (pm + pp);
+        }
+        const float o = cc + wd * ((s - d * cc) - r[p]);
+        eout[p] = o;
+        if (i == 2) eout[p - 1] = o;  // e_1 = e_2
+    }
+}
+
+// r32 = -(L u - b) * scale at the active points (scale: a power of 2).
+template <int ND>
+__global__ void k_sph_defect(srj::Geom g, Coef c, const double* __restrict__ b, const double* __restrict__ u,
+                             double scale, float* __restrict__ r32) {
+    const int64_t na = (int64_t)(g.nx - 1) * g.ny;
+    const int64_t nk = ND == 3 ? g.nz : 1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < na * nk; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kk = t / na, rem = t % na;
+        const int j = 1 + (int)(rem / (g.nx - 1));
+        const int i = 2 + (int)(rem % (g.nx - 1));
+        const int k = ND == 3 ? 1 + (int)kk : 0;
+        const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        double d;
+        r32[p] = (float)(-sph_res<ND>(g, c, b, u, i, j, k, p, &d) * scale);
+    }
+}
+
+// u += e / scale on rows i = 1..n_r (e_1 = e_2 keeps the prescription).
+__global__ void k_sph_update(srj::Geom g, double* __restrict__ u, const float* __restrict__ e, double inv_scale) {
+    const int64_t n = (int64_t)g.nx * g.ny * (g.nd == 3 ? g.nz : 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = 1 + (int)(t % g.nx);
+        const int64_t rest = t / g.nx;
+        const int j = 1 + (int)(rest % g.ny);
+        const int k = g.nd == 3 ? 1 + (int)(rest / g.ny) : 0;
+        const int64_t p = (g.nd == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        u[p] += inv_scale * (double)e[p];
+    }
+}
+
 // Ghost layer and row i = 1 from the prescriptions (the r = 1 ghost is data).
 __global__ void k_sph_fin_r(srj::Geom g, double* __restrict__ u) {  // (j, k): u_1 = u_2, u_0 = u_1
     const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -158,6 +227,13 @@ struct srj_sph_plan {
     double* partials = nullptr;
     double* norms = nullptr;
     double* host_norms = nullptr;
+    int precision = SRJ_PREC_FP64;
+    float* coef32 = nullptr;  // mixed: FP32 copy of the coefficients
+    srj_sph::Coef32 c32{};
+    float* ea = nullptr;      // mixed: FP32 correction (ping-pong) and defect
+    float* eb = nullptr;
+    float* r32 = nullptr;
+    float* e_final = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t cycle = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -181,6 +257,23 @@ cudaError_t launch_sweep(const srj_sph_plan* p, double omega, const double* b, c
              p->nd == 3 ? (unsigned)std::min(p->g.nz, 64) : 1u);
     if (p->nd == 3) k_sph_sweep<3><<<grd, blk, 0, s>>>(p->g, p->c, omega, b, uin, uout);
     else            k_sph_sweep<2><<<grd, blk, 0, s>>>(p->g, p->c, omega, b, uin, uout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_f32(const srj_sph_plan* p, float omega, const float* ein, float* eout, cudaStream_t s) {
+    if (p->g.nx < 2) return cudaSuccess;
+    dim3 blk(128, 2, 1);
+    dim3 grd((unsigned)((p->g.nx - 1 + 127) / 128), (unsigned)((p->g.ny + 1) / 2),
+             p->nd == 3 ? (unsigned)std::min(p->g.nz, 64) : 1u);
+    if (p->nd == 3) k_sph_sweep_f32<3><<<grd, blk, 0, s>>>(p->g, p->c32, omega, p->r32, ein, eout);
+    else            k_sph_sweep_f32<2><<<grd, blk, 0, s>>>(p->g, p->c32, omega, p->r32, ein, eout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_defect(const srj_sph_plan* p, double scale, cudaStream_t s) {
+    if (p->g.nx < 2) return cudaSuccess;
+    if (p->nd == 3) k_sph_defect<3><<<4 * kResBlocks, kResThreads, 0, s>>>(p->g, p->c, p->bb, p->ua, scale, p->r32);
+    else            k_sph_defect<2><<<4 * kResBlocks, kResThreads, 0, s>>>(p->g, p->c, p->bb, p->ua, scale, p->r32);
     return cudaGetLastError();
 }
 
@@ -226,23 +319,36 @@ void destroy(srj_sph_plan* p) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->coef); cudaFree(p->ua); cudaFree(p->ub); cudaFree(p->bb); cudaFree(p->partials);
-    cudaFree(p->norms);
+    cudaFree(p->norms); cudaFree(p->coef32); cudaFree(p->ea); cudaFree(p->eb); cudaFree(p->r32);
     if (p->host_norms) cudaFreeHost(p->host_norms);
     delete p;
 }
 
-// One M-cycle from ua back into ua (an odd M ends with a copy).
+// One M-cycle.  FP64: from ua back into ua (an odd M ends with a copy).
+// Mixed: e = 0, then the FP32 steps on L e = r32; the result is in e_final.
 int capture_cycle(srj_sph_plan* p) {
     cudaGraph_t graph = nullptr;
     SPH_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     const size_t bytes = sizeof(double) * (size_t)p->g.n64;
-    for (size_t k = 0; k < p->seq.size() && err == cudaSuccess; ++k) {
-        const bool from_a = (k % 2) == 0;
-        err = launch_sweep(p, p->seq[k], p->bb, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->cap);
+    if (p->precision == SRJ_PREC_MIXED) {
+        const size_t b32 = sizeof(float) * (size_t)p->g.n64;
+        err = cudaMemsetAsync(p->ea, 0, b32, p->cap);
+        if (err == cudaSuccess) err = cudaMemsetAsync(p->eb, 0, b32, p->cap);
+        float *in = p->ea, *out = p->eb;
+        for (size_t k = 0; k < p->seq.size() && err == cudaSuccess; ++k) {
+            err = launch_sweep_f32(p, (float)p->seq[k], in, out, p->cap);
+            std::swap(in, out);
+        }
+        p->e_final = in;
+    } else {
+        for (size_t k = 0; k < p->seq.size() && err == cudaSuccess; ++k) {
+            const bool from_a = (k % 2) == 0;
+            err = launch_sweep(p, p->seq[k], p->bb, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->cap);
+        }
+        if (err == cudaSuccess && (p->seq.size() % 2) == 1)
+            err = cudaMemcpyAsync(p->ua, p->ub, bytes, cudaMemcpyDeviceToDevice, p->cap);
     }
-    if (err == cudaSuccess && (p->seq.size() % 2) == 1)
-        err = cudaMemcpyAsync(p->ua, p->ub, bytes, cudaMemcpyDeviceToDevice, p->cap);
     cudaError_t e2 = cudaStreamEndCapture(p->cap, &graph);
     if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SPH_CUDA(err); }
     SPH_CUDA(e2);
@@ -298,9 +404,11 @@ int srj_sph_coefficients(int ndim, const int64_t* dims, double* radial, double* 
 
 int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, const double* radial,
                         const double* polar, const double* azim, int P, const double* omega, const int32_t* q,
-                        const int32_t* order) {
+                        const int32_t* order, int precision) {
     if (!out) return sfail(SRJ_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    if (precision != SRJ_PREC_FP64 && precision != SRJ_PREC_MIXED)
+        return sfail(SRJ_ERR_INVALID_ARG, "precision must be SRJ_PREC_FP64 or SRJ_PREC_MIXED");
     if ((ndim != 2 && ndim != 3) || !dims || !radial || !polar || (ndim == 3 && !azim) || !omega || !q)
         return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
     if (P < 1 || P > 32) return sfail(SRJ_ERR_INVALID_ARG, "P must be in 1..32");
@@ -339,6 +447,7 @@ int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, cons
     }
     auto* p = new srj_sph_plan();
     p->nd = ndim;
+    p->precision = precision;
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return sfail(SRJ_ERR_CUDA, "no device"); }
     p->g = srj::make_geom(ndim, dims);
     p->seq.resize((size_t)M);
@@ -367,6 +476,21 @@ int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, cons
     const double* base = p->coef;
     p->c = Coef{base, base + (nr + 2), base + 2 * (nr + 2), base + 3 * (nr + 2), base + 3 * (nr + 2) + (nt + 2),
                 base + 3 * (nr + 2) + 2 * (nt + 2), base + 3 * (nr + 2) + 3 * (nt + 2)};
+    if (precision == SRJ_PREC_MIXED) {
+        std::vector<float> h32(hc.begin(), hc.end());
+        const size_t b32 = sizeof(float) * (size_t)p->g.n64;
+        if (cudaMalloc(&p->coef32, sizeof(float) * ncoef) != cudaSuccess || cudaMalloc(&p->ea, b32) != cudaSuccess ||
+            cudaMalloc(&p->eb, b32) != cudaSuccess || cudaMalloc(&p->r32, b32) != cudaSuccess ||
+            cudaMemcpy(p->coef32, h32.data(), sizeof(float) * ncoef, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(p->r32, 0, b32) != cudaSuccess) {
+            cudaGetLastError();
+            destroy(p);
+            return sfail(SRJ_ERR_CUDA, "plan allocation failed");
+        }
+        const float* b2 = p->coef32;
+        p->c32 = Coef32{b2, b2 + (nr + 2), b2 + 2 * (nr + 2), b2 + 3 * (nr + 2), b2 + 3 * (nr + 2) + (nt + 2),
+                        b2 + 3 * (nr + 2) + 2 * (nt + 2), b2 + 3 * (nr + 2) + 3 * (nt + 2)};
+    }
     int rc = capture_cycle(p);
     if (rc != SRJ_OK) { destroy(p); return rc; }
     *out = p;
@@ -435,9 +559,19 @@ int srj_sph_solve(srj_sph_plan_t p, const double* b, double* u, double tol, int6
     int stall = 0;
     float ms_total = 0.f;
     for (int64_t c = 1; status == SRJ_ERR_NOT_CONVERGED && c <= max_cycles; ++c) {
+        double scale = 1.0;
+        if (p->precision == SRJ_PREC_MIXED) {
+            // defect scaled by a power of 2 so that its largest entry is in [1, 2)
+            scale = (linf > 0.0 && std::isfinite(linf)) ? std::ldexp(1.0, -std::ilogb(linf)) : 1.0;
+            SPH_CUDA(launch_defect(p, scale, s));
+        }
         SPH_CUDA(cudaEventRecord(p->ev0, s));
         SPH_CUDA(cudaGraphLaunch(p->cycle, s));
         SPH_CUDA(cudaEventRecord(p->ev1, s));
+        if (p->precision == SRJ_PREC_MIXED) {
+            k_sph_update<<<4 * kResBlocks, kResThreads, 0, s>>>(p->g, p->ua, p->e_final, 1.0 / scale);
+            SPH_CUDA(cudaGetLastError());
+        }
         SPH_CUDA(launch_residual(p, p->bb, p->ua, nullptr, s));
         rc = read_norms(p, s, &l2, &linf);
         if (rc) return rc;

@@ -1,4 +1,5 @@
-"""SRJ on the spherical-coordinate operators of Sect. 5.2 (FP64, native library).
+"""SRJ on the spherical-coordinate operators of Sect. 5.2 (native library; FP64, or
+FP32 cycles inside FP64 defect correction).
 
 The Poisson equation in (r, theta[, phi]) multiplied by r^2, on cell-centred
 grids over r in [0, 1], theta in [0, pi], phi in [0, 2 pi], with the boundary
@@ -33,9 +34,11 @@ def coefficients(dims):
 
 
 class SphericalPlan:
-    """One spherical grid, its operator coefficients and one SRJ schedule."""
+    """One spherical grid, its operator coefficients and one SRJ schedule;
+    precision "fp64" or "mixed" (FP32 cycles inside FP64 defect correction).
+    ``steps`` applies FP64 steps in either precision."""
 
-    def __init__(self, dims, omega, q, order=None, coef=None):
+    def __init__(self, dims, omega, q, order=None, coef=None, precision="fp64"):
         self.dims = tuple(int(v) for v in dims)
         if len(self.dims) not in (2, 3):
             raise ValueError("dims must be (n_r, n_theta) or (n_r, n_theta, n_phi)")
@@ -55,7 +58,8 @@ class SphericalPlan:
                                             polar.ctypes.data_as(dp),
                                             azim.ctypes.data_as(dp) if azim is not None else None, len(omega),
                                             omega.ctypes.data_as(dp), q.ctypes.data_as(ip),
-                                            ordr.ctypes.data_as(ip) if ordr is not None else None))
+                                            ordr.ctypes.data_as(ip) if ordr is not None else None,
+                                            {"fp64": 0, "mixed": 1}[precision]))
 
     def __del__(self):
         h = getattr(self, "_h", None)

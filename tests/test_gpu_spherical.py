@@ -1,6 +1,7 @@
-"""Parity of the spherical-operator path (Sect. 5.2, FP64) with the oracle:
-sweeps and residual fields bit for bit, solves cycle for cycle, and the paper's
-analytic test at the oracle's discretisation error."""
+"""Parity of the spherical-operator path (Sect. 5.2) with the oracle: FP64
+sweeps and residual fields bit for bit, FP64 solves cycle for cycle, mixed-
+precision solves to tolerance (checked by the oracle's residual), and the
+paper's analytic test at the oracle's discretisation error."""
 import math
 
 import numpy as np
@@ -78,7 +79,27 @@ def test_solve_matches_oracle_cycle_for_cycle(dims):
     assert st["rel_res"] == pytest.approx(so["rel"], rel=1e-10, abs=1e-300)
 
 
-def test_paper_problem_reaches_the_discretisation_error():
+@pytest.mark.parametrize("dims", [(300, 200), (40, 30, 20), (64, 64)])
+def test_mixed_solve_reaches_tolerance(dims):
+    """FP32 cycles inside FP64 defect correction: the oracle's own residual of
+    the returned field meets the tolerance, within a few cycles of FP64."""
+    n = max(dims)
+    row = sch.lookup(2, 256 if n > 128 else 64, 8 if n > 128 else 6)
+    b, u0 = problem(dims, 9)
+    coef = sp.coefficients(dims)
+    r0, _ = oracle.sph_residual(dims, coef, b, u0)
+    mixed = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"], coef=coef, precision="mixed")
+    ud = dev(u0)
+    st = mixed.solve(dev(b), ud, 1e-10, 500)
+    l2, _ = oracle.sph_residual(dims, coef, b, ud.cpu().numpy())
+    assert l2 / r0 <= 1.5e-10
+    fp64 = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"], coef=coef)
+    st64 = fp64.solve(dev(b), dev(u0), 1e-10, 500)
+    assert st["cycles"] <= st64["cycles"] + 3, (st, st64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_problem_reaches_the_discretisation_error(precision):
     """Sect. 5.2 axisymmetric test (l = 0, 2 terms), N = 256: the GPU solve
     reaches the oracle's discretisation error (second order: 1.5e-5)."""
     N = 256
@@ -87,7 +108,7 @@ def test_paper_problem_reaches_the_discretisation_error():
     u0 = np.zeros_like(ua)
     u0[:, -1] = ua[:, -1]
     row = sch.lookup(2, 256, 8)
-    plan = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"])
+    plan = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"], precision=precision)
     ud = dev(u0)
     st = plan.solve(dev(b), ud, 1e-12, 2000)
     u = ud.cpu().numpy()
