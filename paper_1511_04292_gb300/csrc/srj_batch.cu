@@ -55,6 +55,27 @@ constexpr int kPhasesPerGraph = 16;
 
 enum { kFinInit0 = 0, kFinInit1 = 1, kFinCycle = 2 };
 
+// Per-problem arguments of the coming sweep phase (0 steps when inactive).
+__global__ void k_batch_prepare(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
+                                const float* __restrict__ cw, srj::BatchArgs* __restrict__ args, int nprob, int T) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    const srj::BatchState s = st[p];
+    const srj::BatchProb P = probs[p];
+    srj::BatchArgs a;
+    a.n = s.active ? min(T, P.M - s.k) : 0;
+    a.ein = s.cur ? P.eb : P.ea;
+    a.eout = s.cur ? P.ea : P.eb;
+    a.r32 = P.r32;
+    a.p32 = P.p32;
+    a.nx = P.nx;
+    a.ny = P.ny;
+    a.fresh = s.fresh;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a.c[t] = (t < a.n) ? cw[P.c_off + s.k + t] : 0.f;
+    args[p] = a;
+}
+
 __global__ void k_batch_advance(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st, int nprob,
                                 int T) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,6 +221,7 @@ struct srj_batch {
     srj::BatchProb* d_probs = nullptr;
     srj::BatchState* d_state = nullptr;
     int4* d_tiles = nullptr;
+    srj::BatchArgs* d_args = nullptr;
     int2* d_rowblocks = nullptr;
     float* d_cw = nullptr;
     float* d_pool = nullptr;  // all FP32 workspaces
@@ -217,7 +239,7 @@ struct srj_batch {
         if (cap) cudaStreamDestroy(cap);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
-        cudaFree(d_probs); cudaFree(d_state); cudaFree(d_tiles); cudaFree(d_rowblocks);
+        cudaFree(d_probs); cudaFree(d_state); cudaFree(d_tiles); cudaFree(d_rowblocks); cudaFree(d_args);
         cudaFree(d_cw); cudaFree(d_pool); cudaFree(d_partials); cudaFree(d_count);
         if (h_count) cudaFreeHost(h_count);
     }
@@ -227,7 +249,8 @@ namespace {
 
 cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles) {
     const int pb = (b->nprob + kThreads - 1) / kThreads;
-    cudaError_t e = srj::launch_batch_sweep_tb(b->T, (unsigned)b->ntiles, b->d_probs, b->d_state, b->d_tiles, b->d_cw, s);
+    k_batch_prepare<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_cw, b->d_args, b->nprob, b->T);
+    cudaError_t e = srj::launch_batch_sweep_tb(b->T, (unsigned)b->ntiles, b->d_tiles, b->d_args, s);
     if (e != cudaSuccess) return e;
     k_batch_advance<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->nprob, b->T);
     k_batch_update<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks);
@@ -342,6 +365,7 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
               alloc((void**)&b->d_probs, sizeof(srj::BatchProb) * nprob) &&
               alloc((void**)&b->d_state, sizeof(srj::BatchState) * nprob) &&
               alloc((void**)&b->d_tiles, sizeof(int4) * tiles.size()) &&
+              alloc((void**)&b->d_args, sizeof(srj::BatchArgs) * (size_t)nprob) &&
               alloc((void**)&b->d_rowblocks, sizeof(int2) * rowblocks.size()) &&
               alloc((void**)&b->d_cw, sizeof(float) * cw.size()) &&
               alloc((void**)&b->d_partials, sizeof(double) * 2 * rowblocks.size()) &&

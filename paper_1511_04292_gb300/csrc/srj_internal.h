@@ -128,9 +128,21 @@ struct BatchState {
     int stagnated, pad2;
 };
 
+// What one sweep phase needs of a problem, written by k_batch_prepare at the
+// start of the phase so that a sweep block reads one record after its tile.
+struct BatchArgs {
+    const float* ein;      // current correction
+    float* eout;           // next correction
+    const float* r32;      // FP32 defect
+    int64_t p32;           // float32 row pitch
+    int nx, ny;            // interior points
+    int n;                 // steps in this phase (0: inactive)
+    int fresh;             // ein is identically 0
+    float c[8];            // weight / 4 of each step
+};
+
 void tb_tile_shape(int T, int* TX, int* TY);
-cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const BatchProb* probs, const BatchState* st,
-                                  const int4* tiles, const float* cw, cudaStream_t s);
+cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const int4* tiles, const BatchArgs* args, cudaStream_t s);
 
 // Host-side schedule helpers shared by the plan and the batch (srj_plan.cu).
 std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin);

@@ -366,21 +366,91 @@ k_sweep_f32_tbp(const float* __restrict__ ein, const float* __restrict__ rin, fl
 // are skipped.
 template <int T>
 __global__ void __launch_bounds__(kWarps * 32, 2)
-k_batch_sweep_tb(const BatchProb* __restrict__ probs, const BatchState* __restrict__ st,
-                 const int4* __restrict__ tiles, const float* __restrict__ cw) {
+k_batch_sweep_tb(const int4* __restrict__ tiles, const BatchArgs* __restrict__ args) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int TX = kSX - 2 * HX, TY = kSY - 2 * T;
     __shared__ float4 xch[2 * 2 * kWarps * 32];
     const int4 tl = tiles[blockIdx.x];
-    const int p = tl.x;
-    const BatchState s = st[p];
-    if (!s.active) return;
-    const BatchProb P = probs[p];
-    const int n = min(T, P.M - s.k);
-    float cs[8];
+    const BatchArgs* __restrict__ Ap = args + tl.x;
+    struct { const float* ein; float* eout; const float* r32; int64_t p32; int nx, ny, fresh; } A;
+    const int n = Ap->n;
+    if (n == 0) return;  // problem no longer iterating (uniform over the block)
+    A.ein = Ap->ein; A.eout = Ap->eout; A.r32 = Ap->r32; A.p32 = Ap->p32;
+    A.nx = Ap->nx; A.ny = Ap->ny; A.fresh = Ap->fresh;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int X0 = 1 + TX * tl.y - HX, Y0 = 1 + TY * tl.z - T;
+    const int Yw = Y0 + w * kBand;
+    const bool xin = X0 >= 1 && X0 + kSX - 1 <= A.nx;
+    const bool yin = Y0 >= 1 && Y0 + kSY - 1 <= A.ny;
+    const int64_t base = (int64_t)Yw * A.p32 + X0 + 3 + 4 * lane;
+    float4 e[kBand], rr[kBand];
+    bool iny[kBand];
+    if (xin && yin) {
+        const float4* pe = reinterpret_cast<const float4*>(A.ein + base);
+        const float4* pr = reinterpret_cast<const float4*>(A.r32 + base);
+        const int64_t stride = A.p32 / 4;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) cs[t] = (t < n) ? cw[P.c_off + s.k + t] : 0.f;
-    const float* ein = s.cur ? P.eb : P.ea;
-    float* eout = s.cur ? P.ea : P.eb;
-    tile_sweep<T>(ein, P.r32, eout, P.nx, P.ny, P.p32, (int64_t)P.ny + 2, cs, n, tl.y, tl.z, s.fresh != 0, xch);
+        for (int i = 0; i < kBand; ++i) {
+            e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!A.fresh) e[i] = __ldg(pe + i * stride);
+            rr[i] = __ldg(pr + i * stride);
+            iny[i] = true;
+        }
+    } else {
+        const int col = X0 + 3 + 4 * lane;
+        const bool colok = col >= 0 && col + 4 <= A.p32;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int64_t y = (int64_t)Yw + i;
+            e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rr[i] = e[i];
+            if (colok && y >= 0 && y < (int64_t)A.ny + 2) {
+                const int64_t off = y * A.p32 + col;
+                if (!A.fresh) e[i] = __ldg(reinterpret_cast<const float4*>(A.ein + off));
+                rr[i] = __ldg(reinterpret_cast<const float4*>(A.r32 + off));
+            }
+            iny[i] = y >= 1 && y <= A.ny;
+        }
+    }
+    bool inx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int x = X0 + 4 * lane + j;
+        inx[j] = x >= 1 && x <= A.nx;
+    }
+    if (xin && yin) band_steps<T, false, false>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
+    else if (xin)   band_steps<T, true, false>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
+    else if (yin)   band_steps<T, false, true>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
+    else            band_steps<T, true, true>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
+    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+    if (lane < lane_lo || lane >= lane_hi) return;
+    if (xin && yin) {
+        float4* po = reinterpret_cast<float4*>(A.eout + base);
+        const int64_t stride = A.p32 / 4;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            if (row >= T && row < T + TY) po[i * stride] = e[i];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kBand; ++i) {
+        const int row = w * kBand + i;
+        if (row < T || row >= T + TY) continue;
+        const int y = Y0 + row;
+        if (y < 1 || y > A.ny) continue;
+        const int x = X0 + 4 * lane;
+        float* dst = A.eout + (int64_t)y * A.p32 + x + 3;
+        if (inx[0] && inx[3]) {
+            *reinterpret_cast<float4*>(dst) = e[i];
+        } else {
+            if (inx[0]) dst[0] = e[i].x;
+            if (inx[1]) dst[1] = e[i].y;
+            if (inx[2]) dst[2] = e[i].z;
+            if (inx[3]) dst[3] = e[i].w;
+        }
+    }
 }
 
 size_t smem_bytes() { return 0; }
@@ -424,9 +494,8 @@ void launch_W(int T, dim3 grd, cudaStream_t s, const float* ein, const float* ri
 }
 
 template <int T>
-void launch_batch_T(unsigned ntiles, cudaStream_t s, const BatchProb* probs, const BatchState* st, const int4* tiles,
-                    const float* cw) {
-    k_batch_sweep_tb<T><<<ntiles, kWarps * 32, 0, s>>>(probs, st, tiles, cw);
+void launch_batch_T(unsigned ntiles, cudaStream_t s, const int4* tiles, const BatchArgs* args) {
+    k_batch_sweep_tb<T><<<ntiles, kWarps * 32, 0, s>>>(tiles, args);
 }
 
 cudaError_t tb_prepare() {
@@ -478,18 +547,17 @@ void tb_tile_shape(int T, int* TX, int* TY) {
     *TY = kSY - 2 * T;
 }
 
-cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const BatchProb* probs, const BatchState* st,
-                                  const int4* tiles, const float* cw, cudaStream_t s) {
+cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const int4* tiles, const BatchArgs* args, cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
     switch (T) {
-        case 1: launch_batch_T<1>(ntiles, s, probs, st, tiles, cw); break;
-        case 2: launch_batch_T<2>(ntiles, s, probs, st, tiles, cw); break;
-        case 3: launch_batch_T<3>(ntiles, s, probs, st, tiles, cw); break;
-        case 4: launch_batch_T<4>(ntiles, s, probs, st, tiles, cw); break;
-        case 5: launch_batch_T<5>(ntiles, s, probs, st, tiles, cw); break;
-        case 6: launch_batch_T<6>(ntiles, s, probs, st, tiles, cw); break;
-        case 7: launch_batch_T<7>(ntiles, s, probs, st, tiles, cw); break;
-        default: launch_batch_T<8>(ntiles, s, probs, st, tiles, cw); break;
+        case 1: launch_batch_T<1>(ntiles, s, tiles, args); break;
+        case 2: launch_batch_T<2>(ntiles, s, tiles, args); break;
+        case 3: launch_batch_T<3>(ntiles, s, tiles, args); break;
+        case 4: launch_batch_T<4>(ntiles, s, tiles, args); break;
+        case 5: launch_batch_T<5>(ntiles, s, tiles, args); break;
+        case 6: launch_batch_T<6>(ntiles, s, tiles, args); break;
+        case 7: launch_batch_T<7>(ntiles, s, tiles, args); break;
+        default: launch_batch_T<8>(ntiles, s, tiles, args); break;
     }
     return cudaGetLastError();
 }
