@@ -90,12 +90,13 @@ cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* ri
 cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,
                                  const TbSteps& steps, int blocks, cudaStream_t s);
 
-// 3-D: two consecutive FP32 steps (weights c0 then c1) in one launch, by
-// persistent blocks (at most `blocks`, one per SM) streaming z segments of
-// 128 x 32 tiles.  Same bits as two single steps.
-cudaError_t tb3_prepare();  // kernel attribute (dynamic shared memory)
-cudaError_t launch_sweep3_f32_tb2(const Geom& g, const float* ein, const float* rin, float* eout, float c0, float c1,
-                                  int blocks, cudaStream_t s);
+// 3-D: steps.T = 2 or 3 consecutive FP32 steps in one launch, by persistent
+// blocks (at most `blocks`, one per SM) streaming z segments of 128 x 32 tiles.
+// Same bits as steps.T single steps.
+cudaError_t tb3_prepare();  // kernel attributes (dynamic shared memory)
+int tb3_max_steps();
+cudaError_t launch_sweep3_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout, const TbSteps& steps,
+                                 int blocks, cudaStream_t s);
 
 // ---- batched solver (independent 2-D problems, mixed precision) -----------
 

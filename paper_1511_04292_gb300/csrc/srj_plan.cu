@@ -294,9 +294,11 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
         const int n = (int)std::min<int64_t>(T, count - k);
         if (T == 1 || n == 1) {
             err = srj::launch_sweep_f32(p->g, in, out, p->r32, (float)p->c64[(size_t)((first + k) % M)], s, (float)p->diag64, p->mask);
-        } else if (p->g.nd == 3) {  // 3-D: two steps per launch
-            err = srj::launch_sweep3_f32_tb2(p->g, in, p->r32, out, (float)p->c64[(size_t)((first + k) % M)],
-                                             (float)p->c64[(size_t)((first + k + 1) % M)], p->sm_count, s);
+        } else if (p->g.nd == 3) {  // 3-D: 2 or 3 steps per launch, z-streamed tiles
+            srj::TbSteps st{};
+            st.T = n;
+            for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
+            err = srj::launch_sweep3_f32_tb(p->g, in, p->r32, out, st, p->sm_count, s);
         } else {
             srj::TbSteps st{};
             st.T = n;
@@ -369,7 +371,8 @@ int set_depth(srj_plan* p, int T) {
     if (T < 1 || T > srj::tb_max_steps()) return fail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..%d", srj::tb_max_steps());
     if (T > 1 && p->precision != SRJ_PREC_MIXED)
         return fail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for mixed-precision plans");
-    if (T > 2 && p->g.nd == 3) return fail(SRJ_ERR_INVALID_ARG, "3-D plans take temporal depth 1 or 2");
+    if (T > srj::tb3_max_steps() && p->g.nd == 3)
+        return fail(SRJ_ERR_INVALID_ARG, "3-D plans take temporal depth 1..%d", srj::tb3_max_steps());
     if (T > 1 && (p->mask || p->sigma != 0.0))
         return fail(SRJ_ERR_INVALID_ARG, "temporal blocking implements the plain operator (no mask, no shift)");
     p->tdepth = T;
@@ -606,10 +609,10 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     int rc = check_plan(p);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // candidates (T, variant): the unblocked sweep, then the blocked variants for T = 2..8 (2-D) or T = 2 (3-D)
+    // candidates (T, variant): the unblocked sweep, then the blocked variants for T = 2..8 (2-D) or T = 2, 3 (3-D)
     int candT[22] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
     int candV[22] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2};
-    int ncand = (p->precision == SRJ_PREC_MIXED && !p->mask && p->sigma == 0.0) ? (p->g.nd == 2 ? 22 : 2) : 1;
+    int ncand = (p->precision == SRJ_PREC_MIXED && !p->mask && p->sigma == 0.0) ? (p->g.nd == 2 ? 22 : 3) : 1;
     int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;

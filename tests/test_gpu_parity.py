@@ -273,24 +273,25 @@ def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
 
 @pytest.mark.parametrize("dims", [(37, 23, 19), (130, 67, 70), (1, 1, 1), (5, 300, 3), (129, 29, 65), (250, 2, 130)])
 def test_blocked_fp32_sweep_3d_bit_identical_to_single_steps(dims):
-    """3-D temporal blocking (two steps per launch, tiles streamed through z in
-    segments of 64 planes) must give exactly the bits of single-step launches,
-    for even and odd step counts, on grids ragged against the 120 x 28 tile
-    centre and spanning more than one z segment."""
+    """3-D temporal blocking (T = 2 or 3 steps per launch, tiles streamed through
+    z in segments of 64 planes) must give exactly the bits of single-step
+    launches, for step counts that are not multiples of T, on grids ragged
+    against the tile centre and spanning more than one z segment."""
     omega, q, order = small_schedule(dims, 4)
     h = 1.0 / (max(dims) + 1)
     f, u = random_problem(dims, 43)
     u[tuple(slice(1, -1) for _ in dims)] *= 1e-3
     plan = srj.Plan(dims, h, omega, q, order, "mixed")
     fd = dev(f)
-    for count, first in [(len(order), 0), (13, 5), (2, 1)]:
+    for count, first in [(len(order), 0), (13, 5), (2, 1), (3, 2)]:
         plan.set_temporal_depth(1)
         ref = dev(u)
         plan.steps(fd, ref, first, count)
-        plan.set_temporal_depth(2)
-        got = dev(u)
-        plan.steps(fd, got, first, count)
-        assert torch.equal(got, ref), (dims, count, first)
+        for T in (2, 3):
+            plan.set_temporal_depth(T)
+            got = dev(u)
+            plan.steps(fd, got, first, count)
+            assert torch.equal(got, ref), (dims, T, count, first)
 
 
 def test_autotune_picks_a_valid_depth_and_solve_still_converges():
@@ -314,8 +315,9 @@ def test_temporal_depth_rules():
     p3 = srj.Plan((8, 8, 8), 0.1, [1.0], [1], None, "mixed")
     assert p3.temporal_depth() == 2
     p3.set_temporal_depth(1)
+    p3.set_temporal_depth(3)
     with pytest.raises(srj.SRJError):
-        p3.set_temporal_depth(3)
+        p3.set_temporal_depth(4)
     p2 = srj.Plan((16, 16), 0.1, [1.0], [1], None, "mixed")
     assert p2.temporal_depth() == 4
     with pytest.raises(srj.SRJError):
