@@ -54,7 +54,8 @@ extern "C" {
 #define SRJ_ERR_BAD_SCHEDULE  -2  /* integer scheme does not contract on the grid     */
 #define SRJ_ERR_NOT_CONVERGED -3  /* max_cycles reached before tol                   */
 #define SRJ_ERR_DIVERGED      -4  /* residual not finite, or grew by more than 1e6x   */
-#define SRJ_ERR_TIMEOUT       -5  /* a bounded device-side wait gave up               */
+#define SRJ_ERR_TIMEOUT       -5  /* reserved: a bounded device-side wait gave up (no    
+                                     current kernel waits on the device)               */
 #define SRJ_ERR_CUDA          -6  /* a CUDA runtime call failed                      */
 #define SRJ_ERR_NO_MEMORY     -7  /* device or host allocation failed                */
 

@@ -258,8 +258,6 @@ struct srj_plan {
     int variant = 0;     // blocked sweep: 0 = one block per tile, 1 = persistent with cp.async prefetch
     int sm_count = 152;
     float* e_final = nullptr;  // buffer holding the correction after one cycle
-    int* d_err = nullptr;      // set by a kernel whose bounded wait gave up
-    int* host_err = nullptr;   // pinned copy
 
     cudaStream_t cap = nullptr;             // private stream used for graph capture
     cudaGraphExec_t cycle_exec[2] = {nullptr, nullptr};  // start buffer a / b
@@ -273,10 +271,8 @@ struct srj_plan {
         cudaFree(ua); cudaFree(ub); cudaFree(b);
         cudaFree(ea); cudaFree(eb); cudaFree(r32);
         cudaFree(ns.partials); cudaFree(ns.counter); cudaFree(ns.result);
-        cudaFree(d_err);
         cudaFree(mask);
         if (host_norms) cudaFreeHost(host_norms);
-        if (host_err) cudaFreeHost(host_err);
     }
 };
 
@@ -347,14 +343,9 @@ int check_plan(srj_plan_t p) {
 
 int read_norms(srj_plan* p, cudaStream_t s, double* l2, double* linf) {
     SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     *l2 = p->host_norms[0];
     *linf = p->host_norms[1];
-    if (*p->host_err) {
-        cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
-        return fail(SRJ_ERR_TIMEOUT, "a tile load did not complete within its bounded wait");
-    }
     return SRJ_OK;
 }
 
@@ -507,12 +498,9 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
                      cudaMemset(p->r32, 0, by) == cudaSuccess;
     }
     ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 2 * srj::kMaxNormBlocks) &&
-         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double)) &&
-         alloc((void**)&p->d_err, sizeof(int));
+         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double));
     if (!ok) { cudaGetLastError(); return bail(fail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
     if (cudaMemset(p->ns.counter, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&p->host_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&p->host_norms, 2 * sizeof(double)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
@@ -642,9 +630,7 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
         if (ms_best < best) { best = ms_best; bestT = candT[ci]; bestV = candV[ci]; }
     }
     p->variant = bestV;
-    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
-    if (*p->host_err) { cudaMemset(p->d_err, 0, sizeof(int)); return fail(SRJ_ERR_TIMEOUT, "bounded wait gave up"); }
     if (best_T) *best_T = bestT;
     if (best_us_per_step) *best_us_per_step = best * 1000.f / (float)steps;
     return set_depth(p, bestT);
@@ -707,12 +693,7 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
         SRJ_CUDA(issue_f32_steps(p, first, count, s, &fin));
         SRJ_CUDA(srj::launch_from_f32(p->g, fin, u, s));
     }
-    SRJ_CUDA(cudaMemcpyAsync(p->host_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
-    if (*p->host_err) {
-        cudaMemset(p->d_err, 0, sizeof(int));
-        return fail(SRJ_ERR_TIMEOUT, "a tile load did not complete within its bounded wait");
-    }
     return SRJ_OK;
 }
 

@@ -29,10 +29,6 @@ constexpr int kWarps = 8;
 constexpr int kBand = kSY / kWarps;
 constexpr unsigned kTileBytes = kSX * kSY * sizeof(float);
 
-__device__ inline float upd(float c, float two_d, float cc, float nb, float rr) {
-    return fmaf(c, fmaf(-two_d, cc, nb + rr), cc);
-}
-
 // One warp's band of kBand rows lives in registers for all T steps: e[i]
 // (float4, 4 consecutive columns per lane) and the defect rr[i].  Only the
 // band's top and bottom rows cross warps, through a double-buffered shared
@@ -65,9 +61,9 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
             // stale halo of the tile, so what they compute is never stored
             const float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
             const float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            // Single-step update in FP32x2 form: per component the same
-            // operations in the same order as upd() with
-            // nb = ((left + right) + up) + down.  The left + right sums are
+            // Single-step update in FP32x2 form: per component the unblocked
+            // sweep's fmaf(c, fmaf(-4, e, nb + r), e) with
+            // nb = ((left + right) + up) + down, same operations, same order.  The left + right sums are
             // scalar adds whose results land directly in the (x,y) / (z,w)
             // pairs; pairing the misaligned neighbours for a packed add would
             // cost more register moves than the adds it saves.
