@@ -431,6 +431,12 @@ int srj_sph_solve(srj_sph_plan_t plan, const double *b, double *u, double tol, i
 /* Set the ghost layer and row i = 1 of u (device) from the prescriptions. */
 int srj_sph_finalize(srj_sph_plan_t plan, double *u, void *stream);
 
+/* FP32 steps per launch of a mixed 2-D spherical plan (1..8; default 8 when
+ * n_r >= 2): T steps on register-resident tiles give the bits of T single
+ * steps.  Other plans accept only T = 1.  Re-captures the cycle graph. */
+int srj_sph_plan_set_temporal_depth(srj_sph_plan_t plan, int T);
+int srj_sph_plan_temporal_depth(srj_sph_plan_t plan, int *T);
+
 #ifdef __cplusplus
 }
 #endif

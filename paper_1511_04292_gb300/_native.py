@@ -133,6 +133,8 @@ SIGNATURES = {
     "srj_sph_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),
     "srj_sph_solve": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
     "srj_sph_finalize": (_I, [_VP, _VP, _VP]),
+    "srj_sph_plan_set_temporal_depth": (_I, [_VP, _I]),
+    "srj_sph_plan_temporal_depth": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "srj_last_error": (ctypes.c_char_p, []),
     "srj_version": (ctypes.c_char_p, []),
 }

@@ -33,6 +33,8 @@ struct Coef32 {
     const float* cr_m; const float* cr_p; const float* cr_0;
     const float* ct_m; const float* ct_p; const float* ct_0;
     const float* cp;
+    const float* dd;   // 2-D: d_i = cr_0[i] + ct_0 (ct_0 is the same on every polar row)
+    const float* inv;  // 2-D: 1 / d_i
 };
 }  // namespace srj_sph
 
@@ -127,7 +129,12 @@ __global__ void k_sph_norms(const double* __restrict__ partials, int n, double* 
 }
 
 // FP32 step on the defect equation L e = r (mixed precision): the same stencil
-// and prescriptions; e has homogeneous Dirichlet data at r = 1.
+// and prescriptions; e has homogeneous Dirichlet data at r = 1.  FP32 arrays in
+// the pitched layout of the Poisson plans (x stored at column x + 3).  In 2-D
+// every operation is rounded explicitly, in the order
+//   s = (cr_m um + cr_p up) + (ct_m tm + ct_p tp);  t = (s - d e) - r;
+//   e' = e + (omega * (1/d)) t,
+// which the temporally blocked 2-D kernel repeats bit for bit.
 template <int ND>
 __global__ void k_sph_sweep_f32(srj::Geom g, Coef32 c, float omega, const float* __restrict__ r,
                                 const float* __restrict__ ein, float* __restrict__ eout) {
@@ -136,25 +143,168 @@ __global__ void k_sph_sweep_f32(srj::Geom g, Coef32 c, float omega, const float*
     if (i > g.nx || j > g.ny) return;
     const int k0 = ND == 3 ? 1 : 0, k1 = ND == 3 ? g.nz : 0;
     const float crm = c.cr_m[i], crp = c.cr_p[i], ctm = c.ct_m[j], ctp = c.ct_p[j];
-    float d = c.cr_0[i] + c.ct_0[j];
-    if (ND == 3) d += 2.0f * c.cp[j];
-    const float wd = omega / d;
+    float d, wd;
+    if (ND == 3) {
+        d = c.cr_0[i] + c.ct_0[j] + 2.0f * c.cp[j];
+        wd = omega / d;
+    } else {
+        d = c.dd[i];
+        wd = __fmul_rn(omega, c.inv[i]);
+    }
     for (int k = k0 + (int)blockIdx.z; k <= k1; k += (int)gridDim.z) {
-        const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
+        const int64_t p = (ND == 3 ? (int64_t)k * g.plane32 : 0) + (int64_t)j * g.p32 + i + 3;
         const float cc = ein[p];
         const float um = (i == 2) ? cc : ein[p - 1];
         const float up = ein[p + 1];
-        const float tm = (j == 1) ? cc : ein[p - g.sx64];
-        const float tp = (j == g.ny) ? cc : ein[p + g.sx64];
-        float s = (crm * um + crp * up) + (ctm * tm + ctp * tp);
+        const float tm = (j == 1) ? cc : ein[p - g.p32];
+        const float tp = (j == g.ny) ? cc : ein[p + g.p32];
+        float o;
         if (ND == 3) {
-            const float pm = (k == 1) ? ein[p + (int64_t)(g.nz - 1) * g.sy64] : ein[p - g.sy64];
-            const float pp = (k == g.nz) ? ein[p - (int64_t)(g.nz - 1) * g.sy64] : ein[p + g.sy64];
+            float s = (crm * um + crp * up) + (ctm * tm + ctp * tp);
+            const float pm = (k == 1) ? ein[p + (int64_t)(g.nz - 1) * g.plane32] : ein[p - g.plane32];
+            const float pp = (k == g.nz) ? ein[p - (int64_t)(g.nz - 1) * g.plane32] : ein[p + g.plane32];
             s += c.cp[j] * (pm + pp);
+            o = cc + wd * ((s - d * cc) - r[p]);
+        } else {
+            const float s = __fadd_rn(__fadd_rn(__fmul_rn(crm, um), __fmul_rn(crp, up)),
+                                      __fadd_rn(__fmul_rn(ctm, tm), __fmul_rn(ctp, tp)));
+            const float t = __fsub_rn(__fsub_rn(s, __fmul_rn(d, cc)), r[p]);
+            o = __fadd_rn(cc, __fmul_rn(wd, t));
         }
-        const float o = cc + wd * ((s - d * cc) - r[p]);
         eout[p] = o;
         if (i == 2) eout[p - 1] = o;  // e_1 = e_2
+    }
+}
+
+// Temporally blocked form of the 2-D FP32 step: T steps per launch on a
+// 128 x 64 tile held in registers (one float4 of 4 radial points per lane, a
+// band of 8 polar rows per warp, band edges exchanged through shared memory),
+// as the Poisson kernel does; after T steps the centre (128 - 2 HX) x (64 - 2T)
+// is exact.  Each point is updated with the unblocked kernel's expression in
+// its order, including the prescriptions (u_1 = u_2, theta mirrors), so T
+// blocked steps give the bits of T single steps.
+constexpr int kTbX = 128, kTbY = 64, kTbWarps = 8, kTbBand = 8;
+constexpr size_t kTbRsBytes = (size_t)kTbY * 32 * sizeof(float4);  // 32 KB of defect rows
+
+template <int T, bool EDGE>
+__device__ __forceinline__ void sph_band(float4 (&e)[kTbBand], const float4* __restrict__ rs, float4* xch,
+                                         const float2* ctab, const float (&cs)[8], int lane, int w,
+                                         const float (&crm)[4], const float (&crp)[4], const float (&dd)[4],
+                                         const float (&inv)[4], const bool (&act)[4], bool has_x1, int Yw,
+                                         int ny) {
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {  // not unrolled: one step's live set at a time
+        float wd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wd[k] = __fmul_rn(cs[t], inv[k]);
+        float4* slot = xch + (t & 1) * (2 * kTbWarps * 32);
+        slot[(2 * w) * 32 + lane] = e[0];
+        slot[(2 * w + 1) * 32 + lane] = e[kTbBand - 1];
+        __syncthreads();
+        const float4 above = (w > 0) ? slot[(2 * (w - 1) + 1) * 32 + lane] : zero;
+        const float4 below = (w + 1 < kTbWarps) ? slot[(2 * (w + 1)) * 32 + lane] : zero;
+        float4 upr = above;
+#pragma unroll
+        for (int i = 0; i < kTbBand; ++i) {
+            const float4 cur = e[i];
+            const float4 dnr = (i + 1 < kTbBand) ? e[i + 1] : below;
+            const float2 ct = ctab[w * kTbBand + i];
+            const float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            const float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            const float cc[4] = {cur.x, cur.y, cur.z, cur.w};
+            float lt[4] = {lf, cur.x, cur.y, cur.z};
+            const float rg[4] = {cur.y, cur.z, cur.w, rt};
+            float tu[4] = {upr.x, upr.y, upr.z, upr.w};
+            float td[4] = {dnr.x, dnr.y, dnr.z, dnr.w};
+            const float4 rv = rs[(w * kTbBand + i) * 32 + lane];  // this lane's defect row
+            const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
+            const int y = Yw + i;
+            const bool iny = y >= 1 && y <= ny;
+            if (EDGE) {
+                if (has_x1) lt[1] = cc[1];  // radial point 2 sees u(1) = u(2)
+                if (y == 1) { tu[0] = cc[0]; tu[1] = cc[1]; tu[2] = cc[2]; tu[3] = cc[3]; }  // theta mirrors
+                if (y == ny) { td[0] = cc[0]; td[1] = cc[1]; td[2] = cc[2]; td[3] = cc[3]; }
+            }
+            float o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float sv = __fadd_rn(__fadd_rn(__fmul_rn(crm[k], lt[k]), __fmul_rn(crp[k], rg[k])),
+                                           __fadd_rn(__fmul_rn(ct.x, tu[k]), __fmul_rn(ct.y, td[k])));
+                const float tv = __fsub_rn(__fsub_rn(sv, __fmul_rn(dd[k], cc[k])), r4[k]);
+                o[k] = __fadd_rn(cc[k], __fmul_rn(wd[k], tv));
+                if (EDGE && !(iny && act[k])) o[k] = cc[k];
+            }
+            if (EDGE && has_x1 && iny && act[1]) o[0] = o[1];  // u_1 = u_2
+            upr = cur;
+            e[i] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kTbWarps * 32, 2)
+k_sph_tb(srj::Geom g, Coef32 c, srj::TbSteps steps, const float* __restrict__ rin, const float* __restrict__ ein,
+         float* __restrict__ eout) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int TX = kTbX - 2 * HX, TY = kTbY - 2 * T;
+    __shared__ float4 xch[2 * 2 * kTbWarps * 32];
+    __shared__ float2 ctab[kTbY];
+    extern __shared__ float4 rs[];  // [kTbY][32]: the tile's defect rows, each read back by the lane that wrote it
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int X0 = 1 + TX * (int)blockIdx.x - HX, Y0 = 1 + TY * (int)blockIdx.y - T;
+    const int Yw = Y0 + w * kTbBand;
+    if (threadIdx.x < kTbY) {  // polar coefficients of the tile's rows (read after the first barrier)
+        const int y = min(max(Y0 + (int)threadIdx.x, 0), g.ny + 1);
+        ctab[threadIdx.x] = make_float2(c.ct_m[y], c.ct_p[y]);
+    }
+    float crm[4], crp[4], dd[4], inv[4];
+    bool act[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = X0 + 4 * lane + k;
+        const int xc = min(max(x, 0), g.nx + 1);
+        crm[k] = c.cr_m[xc]; crp[k] = c.cr_p[xc]; dd[k] = c.dd[xc]; inv[k] = c.inv[xc];
+        act[k] = x >= 2 && x <= g.nx;
+    }
+    const bool has_x1 = X0 + 4 * lane == 1;  // this lane holds radial points 1 and 2
+    const int col = X0 + 3 + 4 * lane;        // multiple of 4: each float4 wholly in or out of a row
+    const bool colok = col >= 0 && col + 4 <= g.p32;
+    float4 e[kTbBand];
+#pragma unroll
+    for (int i = 0; i < kTbBand; ++i) {
+        const int y = Yw + i;
+        e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 rv = e[i];
+        if (colok && y >= 0 && y <= g.ny + 1) {
+            const int64_t off = (int64_t)y * g.p32 + col;
+            e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+            rv = __ldg(reinterpret_cast<const float4*>(rin + off));
+        }
+        rs[(w * kTbBand + i) * 32 + lane] = rv;
+    }
+    // no prescription, mask or outside point anywhere in the tile
+    const bool interior = X0 >= 3 && X0 + kTbX - 1 <= g.nx && Y0 >= 2 && Y0 + kTbY - 1 <= g.ny - 1;
+    if (interior) sph_band<T, false>(e, rs, xch, ctab, steps.c, lane, w, crm, crp, dd, inv, act, has_x1, Yw, g.ny);
+    else          sph_band<T, true>(e, rs, xch, ctab, steps.c, lane, w, crm, crp, dd, inv, act, has_x1, Yw, g.ny);
+    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+    if (lane < lane_lo || lane >= lane_hi) return;
+#pragma unroll
+    for (int i = 0; i < kTbBand; ++i) {
+        const int row = w * kTbBand + i;
+        if (row < T || row >= T + TY) continue;
+        const int y = Y0 + row;
+        if (y < 1 || y > g.ny) continue;
+        const int x = X0 + 4 * lane;
+        float* dst = eout + (int64_t)y * g.p32 + x + 3;  // 16-byte aligned
+        const float o[4] = {e[i].x, e[i].y, e[i].z, e[i].w};
+        if (x >= 1 && x + 3 <= g.nx) {
+            *reinterpret_cast<float4*>(dst) = e[i];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (x + k >= 1 && x + k <= g.nx) dst[k] = o[k];
+        }
     }
 }
 
@@ -171,7 +321,8 @@ __global__ void k_sph_defect(srj::Geom g, Coef c, const double* __restrict__ b, 
         const int k = ND == 3 ? 1 + (int)kk : 0;
         const int64_t p = (ND == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
         double d;
-        r32[p] = (float)(-sph_res<ND>(g, c, b, u, i, j, k, p, &d) * scale);
+        r32[(ND == 3 ? (int64_t)k * g.plane32 : 0) + (int64_t)j * g.p32 + i + 3] =
+            (float)(-sph_res<ND>(g, c, b, u, i, j, k, p, &d) * scale);
     }
 }
 
@@ -184,7 +335,7 @@ __global__ void k_sph_update(srj::Geom g, double* __restrict__ u, const float* _
         const int j = 1 + (int)(rest % g.ny);
         const int k = g.nd == 3 ? 1 + (int)(rest / g.ny) : 0;
         const int64_t p = (g.nd == 3 ? (int64_t)k * g.sy64 : 0) + (int64_t)j * g.sx64 + i;
-        u[p] += inv_scale * (double)e[p];
+        u[p] += inv_scale * (double)e[(g.nd == 3 ? (int64_t)k * g.plane32 : 0) + (int64_t)j * g.p32 + i + 3];
     }
 }
 
@@ -228,6 +379,7 @@ struct srj_sph_plan {
     double* norms = nullptr;
     double* host_norms = nullptr;
     int precision = SRJ_PREC_FP64;
+    int tdepth = 1;           // mixed 2-D: FP32 steps per blocked launch
     float* coef32 = nullptr;  // mixed: FP32 copy of the coefficients
     srj_sph::Coef32 c32{};
     float* ea = nullptr;      // mixed: FP32 correction (ping-pong) and defect
@@ -267,6 +419,45 @@ cudaError_t launch_sweep_f32(const srj_sph_plan* p, float omega, const float* ei
              p->nd == 3 ? (unsigned)std::min(p->g.nz, 64) : 1u);
     if (p->nd == 3) k_sph_sweep_f32<3><<<grd, blk, 0, s>>>(p->g, p->c32, omega, p->r32, ein, eout);
     else            k_sph_sweep_f32<2><<<grd, blk, 0, s>>>(p->g, p->c32, omega, p->r32, ein, eout);
+    return cudaGetLastError();
+}
+
+template <int T>
+void launch_sph_T(const srj_sph_plan* p, const srj::TbSteps& st, const float* ein, float* eout, cudaStream_t s) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    const int TX = kTbX - 2 * HX, TY = kTbY - 2 * T;
+    dim3 grd((unsigned)((p->g.nx + TX - 1) / TX), (unsigned)((p->g.ny + TY - 1) / TY), 1);
+    k_sph_tb<T><<<grd, kTbWarps * 32, kTbRsBytes, s>>>(p->g, p->c32, st, p->r32, ein, eout);
+}
+
+template <int T>
+cudaError_t sph_tb_attr() {
+    return cudaFuncSetAttribute(k_sph_tb<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTbRsBytes);
+}
+
+cudaError_t sph_tb_prepare() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t r[7] = {sph_tb_attr<2>(), sph_tb_attr<3>(), sph_tb_attr<4>(), sph_tb_attr<5>(),
+                        sph_tb_attr<6>(), sph_tb_attr<7>(), sph_tb_attr<8>()};
+    for (cudaError_t x : r) if (x != cudaSuccess) return x;
+    done = true;
+    return cudaSuccess;
+}
+
+// n = st.T in 2..8 FP32 steps in one launch (2-D mixed plans).
+cudaError_t launch_sweep_f32_tb(const srj_sph_plan* p, const srj::TbSteps& st, const float* ein, float* eout,
+                                cudaStream_t s) {
+    switch (st.T) {
+        case 2: launch_sph_T<2>(p, st, ein, eout, s); break;
+        case 3: launch_sph_T<3>(p, st, ein, eout, s); break;
+        case 4: launch_sph_T<4>(p, st, ein, eout, s); break;
+        case 5: launch_sph_T<5>(p, st, ein, eout, s); break;
+        case 6: launch_sph_T<6>(p, st, ein, eout, s); break;
+        case 7: launch_sph_T<7>(p, st, ein, eout, s); break;
+        case 8: launch_sph_T<8>(p, st, ein, eout, s); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -332,13 +523,23 @@ int capture_cycle(srj_sph_plan* p) {
     cudaError_t err = cudaSuccess;
     const size_t bytes = sizeof(double) * (size_t)p->g.n64;
     if (p->precision == SRJ_PREC_MIXED) {
-        const size_t b32 = sizeof(float) * (size_t)p->g.n64;
+        const size_t b32 = sizeof(float) * (size_t)p->g.n32;
         err = cudaMemsetAsync(p->ea, 0, b32, p->cap);
         if (err == cudaSuccess) err = cudaMemsetAsync(p->eb, 0, b32, p->cap);
         float *in = p->ea, *out = p->eb;
-        for (size_t k = 0; k < p->seq.size() && err == cudaSuccess; ++k) {
-            err = launch_sweep_f32(p, (float)p->seq[k], in, out, p->cap);
+        const size_t M = p->seq.size();
+        for (size_t k = 0; k < M && err == cudaSuccess;) {
+            const int n = (int)std::min<size_t>((size_t)p->tdepth, M - k);
+            if (n >= 2) {
+                srj::TbSteps st{};
+                st.T = n;
+                for (int t = 0; t < n; ++t) st.c[t] = (float)p->seq[k + t];
+                err = launch_sweep_f32_tb(p, st, in, out, p->cap);
+            } else {
+                err = launch_sweep_f32(p, (float)p->seq[k], in, out, p->cap);
+            }
             std::swap(in, out);
+            k += (size_t)n;
         }
         p->e_final = in;
     } else {
@@ -478,10 +679,21 @@ int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, cons
                 base + 3 * (nr + 2) + 2 * (nt + 2), base + 3 * (nr + 2) + 3 * (nt + 2)};
     if (precision == SRJ_PREC_MIXED) {
         std::vector<float> h32(hc.begin(), hc.end());
-        const size_t b32 = sizeof(float) * (size_t)p->g.n64;
-        if (cudaMalloc(&p->coef32, sizeof(float) * ncoef) != cudaSuccess || cudaMalloc(&p->ea, b32) != cudaSuccess ||
+        // 2-D: per-radius diagonal and its reciprocal in FP32 (the polar diagonal
+        // ct_0 = 2 / dtheta^2 is the same on every row)
+        const float ct0 = (float)polar[2 * (nt + 2) + 1];
+        for (int64_t i = 0; i < nr + 2; ++i) {
+            const float d = (float)radial[2 * (nr + 2) + i] + ct0;
+            h32.push_back(d);
+        }
+        for (int64_t i = 0; i < nr + 2; ++i) {
+            const float d = h32[ncoef + (size_t)i];
+            h32.push_back(d != 0.0f ? 1.0f / d : 0.0f);
+        }
+        const size_t b32 = sizeof(float) * (size_t)p->g.n32;
+        if (cudaMalloc(&p->coef32, sizeof(float) * h32.size()) != cudaSuccess || cudaMalloc(&p->ea, b32) != cudaSuccess ||
             cudaMalloc(&p->eb, b32) != cudaSuccess || cudaMalloc(&p->r32, b32) != cudaSuccess ||
-            cudaMemcpy(p->coef32, h32.data(), sizeof(float) * ncoef, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p->coef32, h32.data(), sizeof(float) * h32.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(p->r32, 0, b32) != cudaSuccess) {
             cudaGetLastError();
             destroy(p);
@@ -489,7 +701,16 @@ int srj_sph_plan_create(srj_sph_plan_t* out, int ndim, const int64_t* dims, cons
         }
         const float* b2 = p->coef32;
         p->c32 = Coef32{b2, b2 + (nr + 2), b2 + 2 * (nr + 2), b2 + 3 * (nr + 2), b2 + 3 * (nr + 2) + (nt + 2),
-                        b2 + 3 * (nr + 2) + 2 * (nt + 2), b2 + 3 * (nr + 2) + 3 * (nt + 2)};
+                        b2 + 3 * (nr + 2) + 2 * (nt + 2), b2 + 3 * (nr + 2) + 3 * (nt + 2), b2 + ncoef,
+                        b2 + ncoef + (nr + 2)};
+        if (ndim == 2 && nr >= 2) {
+            if (sph_tb_prepare() != cudaSuccess) {
+                cudaGetLastError();
+                destroy(p);
+                return sfail(SRJ_ERR_CUDA, "set-up of the blocked spherical sweep failed");
+            }
+            p->tdepth = 8;
+        }
     }
     int rc = capture_cycle(p);
     if (rc != SRJ_OK) { destroy(p); return rc; }
@@ -597,6 +818,25 @@ int srj_sph_solve(srj_sph_plan_t p, const double* b, double* u, double tol, int6
     if (stats) *stats = st;
     if (status == SRJ_ERR_NOT_CONVERGED) return sfail(status, "tolerance not reached");
     if (status == SRJ_ERR_DIVERGED) return sfail(status, "residual diverged");
+    return SRJ_OK;
+}
+
+int srj_sph_plan_set_temporal_depth(srj_sph_plan_t p, int T) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (T < 1 || T > 8) return sfail(SRJ_ERR_INVALID_ARG, "temporal depth must be in 1..8");
+    if (T > 1 && !(p->precision == SRJ_PREC_MIXED && p->nd == 2 && p->g.nx >= 2))
+        return sfail(SRJ_ERR_INVALID_ARG, "temporal blocking is available for 2-D mixed-precision plans with n_r >= 2");
+    p->tdepth = T;
+    if (p->cycle) { cudaGraphExecDestroy(p->cycle); p->cycle = nullptr; }
+    return capture_cycle(p);
+}
+
+int srj_sph_plan_temporal_depth(srj_sph_plan_t p, int* T) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!T) return sfail(SRJ_ERR_INVALID_ARG, "T is NULL");
+    *T = p->tdepth;
     return SRJ_OK;
 }
 

@@ -91,6 +91,15 @@ class SphericalPlan:
                                          ctypes.byref(l2), ctypes.byref(linf), _stream_ptr(stream)))
         return l2.value, linf.value
 
+    def set_temporal_depth(self, T):
+        """FP32 steps per blocked launch (mixed 2-D plans: 1..8)."""
+        check(self._lib.srj_sph_plan_set_temporal_depth(self._h, int(T)))
+
+    def temporal_depth(self):
+        out = ctypes.c_int()
+        check(self._lib.srj_sph_plan_temporal_depth(self._h, ctypes.byref(out)))
+        return out.value
+
     def finalize(self, u, stream=None):
         check(self._lib.srj_sph_finalize(self._h, _dev_ptr(u, self.shape, "u", True), _stream_ptr(stream)))
         return u

@@ -127,3 +127,37 @@ def test_bad_schedule_and_bad_arguments_are_rejected():
     plan = sp.SphericalPlan((8, 8), [1.0], [1])
     with pytest.raises(Exception):
         plan.solve(dev(np.zeros((10, 10))), dev(np.zeros((9, 10))), 1e-8, 10)
+
+
+@pytest.mark.parametrize("dims", [(300, 200), (37, 23), (2, 5), (130, 67), (129, 200), (1000, 9)])
+def test_blocked_fp32_cycles_bit_identical(dims):
+    """Mixed 2-D plans run their FP32 cycles T steps per launch on register-
+    resident tiles; T = 3 and 8 must give the bits of single steps (three
+    cycles, ragged grids, tiles holding the r = 0 prescription and the theta
+    mirrors)."""
+    row = sch.lookup(2, 64, 6)
+    b, u0 = problem(dims, 13)
+    plan = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"], precision="mixed")
+    assert plan.temporal_depth() == 8
+    outs = []
+    for T in (1, 3, 8):
+        plan.set_temporal_depth(T)
+        ud = dev(u0)
+        st = plan.solve(dev(b), ud, 1e-30, 3, check_status=False)
+        assert st["cycles"] == 3
+        outs.append(ud.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_spherical_temporal_depth_rules():
+    row = sch.lookup(2, 64, 5)
+    p64 = sp.SphericalPlan((16, 16), row["omega"], row["q"], row["order"])
+    assert p64.temporal_depth() == 1
+    with pytest.raises(Exception):
+        p64.set_temporal_depth(2)
+    p3 = sp.SphericalPlan((8, 8, 8), row["omega"], row["q"], row["order"], precision="mixed")
+    with pytest.raises(Exception):
+        p3.set_temporal_depth(2)
+    p2 = sp.SphericalPlan((16, 16), row["omega"], row["q"], row["order"], precision="mixed")
+    with pytest.raises(Exception):
+        p2.set_temporal_depth(9)
