@@ -238,7 +238,9 @@ int srj_schedule_check(int P, const double *omega, const int32_t *q, double kapp
 /*
  * srj_schedule_order -- host-only: the cycle order srj_plan_create uses when
  * its `order` argument is NULL (M = sum q_i level indices written to
- * order_out).  Needs no GPU.
+ * order_out): the drift order (running log-products kept near their straight
+ * line), ending with copies of the smallest weight, as many as minimise a model
+ * of the FP32 rounding noise of one cycle.  Needs no GPU.
  */
 int srj_schedule_order(int P, const double *omega, const int32_t *q, double kappa_min, int32_t *order_out);
 

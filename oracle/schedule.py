@@ -356,6 +356,69 @@ def order_drift(omega, q, kappa_m, kappa_max=KAPPA_MAX, grids=DRIFT_GRIDS, tail=
     return np.concatenate([body, np.full(k, P - 1, dtype=np.int64)])
 
 
+def fp32_cycle_noise(omega, order, kappa_m, kappa_max=KAPPA_MAX, samples=1024):
+    """Model of the FP32 rounding noise that one cycle leaves in the residual,
+    relative to a white initial residual (used to order the cycle for FP32).
+
+    In the eigenbasis of D^-1 A the correction of a cycle that starts at e = 0
+    is, after step k, e_k(kappa) = (1 - prod_{j<=k} (1 - w_j kappa)) / kappa per
+    unit of residual.  Rounding at step k adds noise of size eps |e_k| spread
+    over all modes; the remaining steps multiply it by the suffix product
+    S_k(kappa) = prod_{j>k} (1 - w_j kappa) and the operator maps it into the
+    residual with a factor kappa.  Returns
+        eps * sqrt( sum_k <e_k^2> <kappa^2 S_k(kappa)^2> ),
+    <.> the mean over `samples` evenly spaced kappa in [kappa_m, kappa_max],
+    eps = 2^-24 (inf if a product overflows)."""
+    w = np.asarray(omega, dtype=np.float64)[np.asarray(order)]
+    kap = np.linspace(kappa_m, kappa_max, samples)
+    M = len(w)
+    back = np.empty(M)
+    S = np.ones(samples)
+    for k in range(M - 1, -1, -1):
+        back[k] = np.mean((kap * S) ** 2)
+        S = S * (1.0 - w[k] * kap)
+        if not np.all(np.isfinite(S)):
+            return math.inf
+    Pf = np.ones(samples)
+    total = 0.0
+    for k in range(M):
+        Pf = Pf * (1.0 - w[k] * kap)
+        total += np.mean(((1.0 - Pf) / kap) ** 2) * back[k]
+        if not math.isfinite(total):
+            return math.inf
+    return 2.0 ** -24 * math.sqrt(total)
+
+
+def order_fp32(omega, q, kappa_m, kappa_max=KAPPA_MAX, moves=range(0, 26, 2)):
+    """Cycle order for FP32 cycles: the drift order (``order_drift``, tail of 4
+    steps of omega_P) with the first m copies of omega_P moved from the body to
+    the tail, m chosen to minimise ``fp32_cycle_noise``.  Moving small weights
+    from the start of the cycle (where the correction is still small) to the end
+    damps the noise made late in the cycle; moving too many unbalances the body
+    and the noise explodes, so m is backed off while m + 4 would more than double
+    the noise.  Every order of the same weights has the same cycle polynomial
+    (Sect. 2): only rounding differs."""
+    base = order_drift(omega, q, kappa_m, kappa_max)
+    P = len(q)
+    if P < 2:
+        return base
+    small = P - 1
+    body = [int(v) for v in base[:-min(TAIL_STEPS, int(q[-1]))]] if q[-1] > 0 else [int(v) for v in base]
+    pos = [i for i, v in enumerate(body) if v == small]
+    tail0 = len(base) - len(body)
+
+    def cand(m):
+        drop = set(pos[:m])
+        return np.array([v for i, v in enumerate(body) if i not in drop] + [small] * (tail0 + m), dtype=np.int64)
+
+    ms = [m for m in moves if m <= len(pos)]
+    noise = {m: fp32_cycle_noise(omega, cand(m), kappa_m, kappa_max) for m in ms}
+    best = min(ms, key=lambda m: noise[m])
+    while best > 0 and (best + 4) in noise and noise[best + 4] > 2.0 * noise[best]:
+        best -= 2
+    return cand(best)
+
+
 def window_growth(omega, order, kappa_m, kappa_max=KAPPA_MAX, samples=2000):
     """Largest growth (log10) of any contiguous run of steps of one cycle,
     max over kappa of max_{a<=b} |prod_{a<j<=b} (1 - omega_j kappa)|, and the

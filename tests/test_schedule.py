@@ -144,6 +144,26 @@ def test_drift_order_is_a_valid_cycle_with_bounded_growth(P, N):
     assert w_even > window + 3.0
 
 
+def test_fp32_order_is_a_valid_cycle_with_no_more_modelled_noise():
+    """order_fp32 permutes the same multiset as the drift order (same cycle
+    polynomial, Sect. 2) and never raises the modelled FP32 cycle noise; an
+    order that moves many small weights out of the body is flagged."""
+    km = oracle.kappa_min_dirichlet((4096, 4096))
+    row = __import__("paper_1511_04292_gb300").schedules.lookup(2, 4096, 10)
+    omega, q = row["omega"], row["q"]
+    base = S.order_drift(omega, q, km)
+    tuned = S.order_fp32(omega, q, km)
+    assert np.bincount(tuned, minlength=len(q)).tolist() == list(q)
+    assert np.array_equal(np.sort(base), np.sort(tuned))
+    nb, nt = S.fp32_cycle_noise(omega, base, km), S.fp32_cycle_noise(omega, tuned, km)
+    assert nt <= nb
+    # 28 of the smallest weights pulled out of the start of the body: unbalanced
+    body = list(base[:-4])
+    drop = set([i for i, v in enumerate(body) if v == len(q) - 1][:28])
+    bad = np.array([v for i, v in enumerate(body) if i not in drop] + [len(q) - 1] * 32)
+    assert S.fp32_cycle_noise(omega, bad, km) > 1.0
+
+
 def test_integer_scheme_contracts():
     """Sect. 4.3: after the floor conversion the cycle factor stays below 1 on
     [kappa_m, 2]; a scheme that over-weights the largest omega does not."""
