@@ -33,13 +33,14 @@ constexpr int kWarps = 16;
 constexpr int kY = 2 * kWarps;          // tile rows: 2 per warp
 constexpr int kHX = 4;                  // x halo: T <= 4 steps rounded up to a float4
 constexpr int kTX = kX - 2 * kHX;       // 120 centre columns
-constexpr int kERing = 4;               // e planes p-1 .. p+2
 constexpr int kZSeg = 64;               // output planes per work item
 constexpr int kPlane = kY * 32;         // float4 per plane tile
 template <int T> struct Cfg {
+    static constexpr int kD = 2;                     // planes loaded ahead of use (3 measured no faster)
+    static constexpr int kERing = kD + 2;            // e planes p-1 .. p+D
     static constexpr int kHY = T;                    // y halo
     static constexpr int kTY = kY - 2 * T;           // centre rows
-    static constexpr int kRRing = T + 3;             // defect planes p-T .. p+2
+    static constexpr int kRRing = T + 1 + kD;        // defect planes p-T .. p+D
     static constexpr int kLSlots = 2 * (T - 1);      // levels 1..T-1, two planes each
     static constexpr size_t kSmem = (size_t)(kERing + kRRing + kLSlots) * kPlane * sizeof(float4);
 };
@@ -49,7 +50,8 @@ __device__ inline void cp_async16(void* smem_dst, const void* gsrc, unsigned src
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
 }
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ inline void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait_pending() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // One 7-point update of 4 consecutive points, in the unblocked kernel's order:
@@ -110,6 +112,7 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
                 TbSteps steps, int tiles_x, int tiles_y, int nseg) {
     using C = Cfg<T>;
     extern __shared__ float4 smem[];
+    constexpr int kERing = C::kERing;
     float4* E = smem;                          // [kERing][kPlane]   level-0 e planes
     float4* R = E + kERing * kPlane;           // [kRRing][kPlane]   defect planes
     float4* L = R + C::kRRing * kPlane;        // [T-1][2][kPlane]   published level planes
@@ -152,8 +155,8 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
             }
             cp_async_commit();  // possibly empty: keeps one group per iteration
         };
-        issue(0);
-        issue(1);
+#pragma unroll
+        for (int d = 0; d < C::kD; ++d) issue(d);
         // this thread's rows of the planes still needed: lv_bk / lv_cc[s] = level s on planes p-s-2 / p-s-1
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 lv_bk[T][2], lv_cc[T][2];
@@ -163,9 +166,9 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
             lv_cc[s][0] = lv_cc[s][1] = z4;
         }
         for (int i = 0; i < niter; ++i) {
-            cp_async_wait_1();  // this thread's loads of iteration i have landed
+            cp_async_wait_pending<C::kD - 1>();  // this thread's loads of iteration i have landed
             __syncthreads();    // ... and everyone's; iteration i-1 is fully done
-            issue(i + 2);       // into slots no longer read
+            issue(i + C::kD);   // into slots no longer read
             const int p = zs - T + i;
             float4 fr[2];       // level s-1 on plane p-s+1: the stage's front plane
             const float4* Ep = E + (i % kERing) * kPlane;
