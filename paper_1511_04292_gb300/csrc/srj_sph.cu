@@ -131,9 +131,9 @@ __global__ void k_sph_norms(const double* __restrict__ partials, int n, double* 
 // FP32 step on the defect equation L e = r (mixed precision): the same stencil
 // and prescriptions; e has homogeneous Dirichlet data at r = 1.  FP32 arrays in
 // the pitched layout of the Poisson plans (x stored at column x + 3).  In 2-D
-// every operation is rounded explicitly, in the order
-//   s = (cr_m um + cr_p up) + (ct_m tm + ct_p tp);  t = (s - d e) - r;
-//   e' = e + (omega * (1/d)) t,
+// every operation is rounded explicitly, in the order (fma: one rounding)
+//   s = fma(cr_m, um, cr_p up) + fma(ct_m, tm, ct_p tp);  t = fma(-d, e, s) - r;
+//   e' = fma(omega * (1/d), t, e),
 // which the temporally blocked 2-D kernel repeats bit for bit.
 template <int ND>
 __global__ void k_sph_sweep_f32(srj::Geom g, Coef32 c, float omega, const float* __restrict__ r,
@@ -166,10 +166,9 @@ __global__ void k_sph_sweep_f32(srj::Geom g, Coef32 c, float omega, const float*
             s += c.cp[j] * (pm + pp);
             o = cc + wd * ((s - d * cc) - r[p]);
         } else {
-            const float s = __fadd_rn(__fadd_rn(__fmul_rn(crm, um), __fmul_rn(crp, up)),
-                                      __fadd_rn(__fmul_rn(ctm, tm), __fmul_rn(ctp, tp)));
-            const float t = __fsub_rn(__fsub_rn(s, __fmul_rn(d, cc)), r[p]);
-            o = __fadd_rn(cc, __fmul_rn(wd, t));
+            const float s = __fadd_rn(__fmaf_rn(crm, um, __fmul_rn(crp, up)), __fmaf_rn(ctm, tm, __fmul_rn(ctp, tp)));
+            const float t = __fsub_rn(__fmaf_rn(-d, cc, s), r[p]);
+            o = __fmaf_rn(wd, t, cc);
         }
         eout[p] = o;
         if (i == 2) eout[p - 1] = o;  // e_1 = e_2
@@ -226,14 +225,31 @@ __device__ __forceinline__ void sph_band(float4 (&e)[kTbBand], const float4* __r
                 if (y == 1) { tu[0] = cc[0]; tu[1] = cc[1]; tu[2] = cc[2]; tu[3] = cc[3]; }  // theta mirrors
                 if (y == ny) { td[0] = cc[0]; td[1] = cc[1]; td[2] = cc[2]; td[3] = cc[3]; }
             }
+            // per point the unblocked kernel's operations in its order; the radial
+            // terms (misaligned neighbours) in scalar form, the rest as FP32x2 pairs
+            // (every multiply-add is an explicit fma, so nothing is left to contract)
+            float hr[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hr[k] = __fmaf_rn(crm[k], lt[k], __fmul_rn(crp[k], rg[k]));
+            const float2 ctm2 = make_float2(ct.x, ct.x), ctp2 = make_float2(ct.y, ct.y);
             float o[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float sv = __fadd_rn(__fadd_rn(__fmul_rn(crm[k], lt[k]), __fmul_rn(crp[k], rg[k])),
-                                           __fadd_rn(__fmul_rn(ct.x, tu[k]), __fmul_rn(ct.y, td[k])));
-                const float tv = __fsub_rn(__fsub_rn(sv, __fmul_rn(dd[k], cc[k])), r4[k]);
-                o[k] = __fadd_rn(cc[k], __fmul_rn(wd[k], tv));
-                if (EDGE && !(iny && act[k])) o[k] = cc[k];
+            for (int h = 0; h < 2; ++h) {
+                const int a = 2 * h, b = 2 * h + 1;
+                const float2 c2 = make_float2(cc[a], cc[b]);
+                const float2 vt = __ffma2_rn(ctm2, make_float2(tu[a], tu[b]),
+                                             __fmul2_rn(ctp2, make_float2(td[a], td[b])));
+                const float2 sv = __fadd2_rn(make_float2(hr[a], hr[b]), vt);
+                const float2 tv = __fadd2_rn(__ffma2_rn(make_float2(-dd[a], -dd[b]), c2, sv),
+                                             make_float2(-r4[a], -r4[b]));
+                const float2 ov = __ffma2_rn(make_float2(wd[a], wd[b]), tv, c2);
+                o[a] = ov.x;
+                o[b] = ov.y;
+            }
+            if (EDGE) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!(iny && act[k])) o[k] = cc[k];
             }
             if (EDGE && has_x1 && iny && act[1]) o[0] = o[1];  // u_1 = u_2
             upr = cur;
