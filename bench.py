@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 3-D 512^3 and batched secondary measurements")
-    ap.add_argument("--kernel-case", choices=["f32", "f64", "sph"], default=None,
+    ap.add_argument("--kernel-case", choices=["f32", "f64", "sph", "sphmix"], default=None,
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
                          "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
@@ -74,6 +74,16 @@ def run_kernel_case(args):
     n = args.n
     torch.cuda.set_device(0)
     dims = (n,) * args.ndim
+    if args.kernel_case == "sphmix":  # one mixed-precision cycle of the Sect. 5.2 test (blocked FP32 sweeps)
+        from paper_1511_04292_gb300 import spherical as sp
+        b_h, u0_h = W.spherical_problem_2d(n, 5)
+        row = srj.schedules.lookup(2, n, 10) if (2, n, 10) in srj.schedules.available() else \
+            srj.schedules.lookup(2, 1024, 10)
+        splan = sp.SphericalPlan((n, n), row["omega"], row["q"], row["order"], precision="mixed")
+        splan.solve(torch.from_numpy(b_h).cuda(), torch.from_numpy(u0_h).cuda(), 1e-30, 1, check_status=False)
+        torch.cuda.synchronize()
+        print("kernel case sphmix n=%d done" % n)
+        return 0
     if args.kernel_case == "sph":
         from paper_1511_04292_gb300 import spherical as sp
         splan = sp.SphericalPlan(dims, [1.0], [1])
