@@ -129,7 +129,7 @@ def test_bad_schedule_and_bad_arguments_are_rejected():
         plan.solve(dev(np.zeros((10, 10))), dev(np.zeros((9, 10))), 1e-8, 10)
 
 
-@pytest.mark.parametrize("dims", [(300, 200), (37, 23), (2, 5), (130, 67), (129, 200), (1000, 9)])
+@pytest.mark.parametrize("dims", [(300, 200), (37, 23), (2, 5), (130, 67), (129, 200), (1000, 9), (3, 1), (200, 1), (121, 2)])
 def test_blocked_fp32_cycles_bit_identical(dims):
     """Mixed 2-D plans run their FP32 cycles T steps per launch on register-
     resident tiles; T = 3 and 8 must give the bits of single steps (three
