@@ -230,6 +230,40 @@ def secondary_workloads(stream):
         speedup_vs_fp64_time_to_tol=res["fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"])
     del bs, us0, us
     torch.cuda.empty_cache()
+    # adjoint (gradient of L = 1/2 ||u - u_t||^2 w.r.t. f and the Dirichlet data), 2048^2, FP64, P = 10
+    from paper_1511_04292_gb300.autograd import srj_solve
+    na = 2048
+    fa_h, ga_h = W.random_smooth_problem_2d(na, 6)
+    ta = torch.from_numpy(W.smooth_target_2d(na, 7)).cuda()
+    fa = torch.from_numpy(fa_h).cuda().requires_grad_(True)
+    ga = torch.from_numpy(ga_h).cuda().requires_grad_(True)
+    aplan = srj.Plan.from_table((na, na), 10, "fp64")
+    # untimed: the same expression on a 64^2 problem loads PyTorch's own kernels (loss, autograd)
+    wplan = srj.Plan.from_table((64, 64), 5, "fp64")
+    wf = torch.zeros(66, 66, dtype=torch.float64, device="cuda", requires_grad=True)
+    wg = torch.zeros(66, 66, dtype=torch.float64, device="cuda", requires_grad=True)
+    (0.5 * ((srj_solve(wf, wg, wplan, 1e-10, 50) - ta[:66, :66])[1:-1, 1:-1] ** 2).sum()).backward()
+    del wplan, wf, wg
+    torch.cuda.synchronize()
+    ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    ea.record(stream)
+    ua = srj_solve(fa, ga, aplan, 1e-10, 400)
+    loss = 0.5 * ((ua - ta)[1:-1, 1:-1] ** 2).sum()
+    eb.record(stream)
+    loss.backward()
+    ec.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = ea.elapsed_time(eb), eb.elapsed_time(ec)
+    fstats = ua.grad_fn.stats
+    bstats = ua.grad_fn.adjoint_stats
+    upd = (fstats["sweeps"] + bstats["sweeps"]) * na * na
+    out["adjoint_2d_2048x2048_P10_fp64_tol1e-10"] = {
+        "forward_s": fwd_ms / 1e3, "backward_s": bwd_ms / 1e3, "time_s": (fwd_ms + bwd_ms) / 1e3,
+        "gupdates_per_s": upd / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "forward_cycles": fstats["cycles"],
+        "adjoint_cycles": bstats["cycles"], "adjoint_rel_residual": bstats["rel_res"],
+        "sweep_kernel": "k_sweep_f64<2>"}
+    del fa, ga, ta, ua, loss, aplan
+    torch.cuda.empty_cache()
     # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10
     specs = W.batch_specs()
     probs, fs, u0s = [], [], []
