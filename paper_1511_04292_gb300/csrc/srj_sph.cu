@@ -452,12 +452,15 @@ cudaError_t sph_tb_attr() {
 }
 
 cudaError_t sph_tb_prepare() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    // kernel attributes are per device: set them once on each device used
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (done[dev]) return cudaSuccess;
     cudaError_t r[7] = {sph_tb_attr<2>(), sph_tb_attr<3>(), sph_tb_attr<4>(), sph_tb_attr<5>(),
                         sph_tb_attr<6>(), sph_tb_attr<7>(), sph_tb_attr<8>()};
     for (cudaError_t x : r) if (x != cudaSuccess) return x;
-    done = true;
+    done[dev] = true;
     return cudaSuccess;
 }
 

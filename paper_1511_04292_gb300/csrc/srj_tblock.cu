@@ -495,13 +495,16 @@ void launch_batch_T(unsigned ntiles, cudaStream_t s, const int4* tiles, const Ba
 }
 
 cudaError_t tb_prepare() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    // kernel attributes are per device: set them once on each device used
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (done[dev]) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     cudaError_t r[8] = {set_attr<1>(), set_attr<2>(), set_attr<3>(), set_attr<4>(),
                         set_attr<5>(), set_attr<6>(), set_attr<7>(), set_attr<8>()};
     for (cudaError_t x : r) if (x != cudaSuccess) e = x;
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 

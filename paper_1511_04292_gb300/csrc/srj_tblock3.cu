@@ -230,13 +230,16 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
 }  // namespace
 
 cudaError_t tb3_prepare() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    // kernel attributes are per device: set them once on each device used
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (done[dev]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_sweep3_f32_tb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<2>::kSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep3_f32_tb<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::kSmem);
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
