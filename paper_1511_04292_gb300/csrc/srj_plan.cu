@@ -800,6 +800,8 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
     int rc = SRJ_OK;
     if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
     if (!(tol >= 0.0) || max_cycles < 0) return fail(SRJ_ERR_INVALID_ARG, "tol must be >= 0 and max_cycles >= 0");
+    if (!p->cycle_exec[0] || (p->precision == SRJ_PREC_FP64 && (p->M % 2) == 1 && !p->cycle_exec[1]))
+        return fail(SRJ_ERR_CUDA, "the plan has no cycle graph (a failed re-capture)");
     cudaStream_t s = (cudaStream_t)stream;
     srj_stats_t st{};
     const size_t by64 = sizeof(double) * (size_t)p->g.n64;

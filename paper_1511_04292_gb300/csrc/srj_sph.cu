@@ -782,6 +782,7 @@ int srj_sph_solve(srj_sph_plan_t p, const double* b, double* u, double tol, int6
     int rc = check_plan(p);
     if (rc) return rc;
     if (!b || !u || !(tol >= 0.0) || max_cycles < 0) return sfail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    if (!p->cycle) return sfail(SRJ_ERR_CUDA, "the plan has no cycle graph (a failed re-capture)");
     cudaStream_t s = (cudaStream_t)stream;
     srj_stats_t st{};
     rc = load_inputs(p, b, u, s);
