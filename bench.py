@@ -222,10 +222,16 @@ def secondary_workloads(stream):
         ms = a.elapsed_time(b)
         res[prec] = dict(time_to_tol_s=ms / 1e3, gupdates_per_s=st["sweeps"] * act / (ms / 1e3) / 1e9,
                          cycles=st["cycles"], final_rel_residual=st["rel_res"],
-                         sweep_gbs=(12.0 if prec == "mixed" else 24.0) * act * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9)
+                         effective_gbs_per_step=(12.0 if prec == "mixed" else 24.0) * act * st["sweeps"]
+                         / (st["sweep_ms"] / 1e3) / 1e9)
+        if prec == "mixed":
+            T = splan.temporal_depth()
+            res[prec]["temporal_depth"] = T
+            res[prec]["sweep_kernel"] = (f"k_sph_tb<{T}> ({T} FP32 steps per launch, FP64 correction)" if T > 1
+                                         else "k_sph_sweep_f32<2> (FP32 cycles, FP64 correction)")
         del splan
     out["spherical_2d_1024x1024_P10_mixed_tol1e-10"] = dict(
-        res["mixed"], sweep_kernel="k_sph_sweep_f32<2> (FP32 cycles, FP64 correction)",
+        res["mixed"],
         fp64_comparator=dict(res["fp64"], sweep_kernel="k_sph_sweep<2> (FP64)"),
         speedup_vs_fp64_time_to_tol=res["fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"])
     del bs, us0, us
