@@ -246,6 +246,58 @@ def test_full_size_workload2_mixed_solve():
     assert np.all(np.abs(got - ref)[1:-1, 1:-1] <= bound[1:-1, 1:-1])
 
 
+def test_full_size_workload3_mixed_solve():
+    """Workload 3 at full size (512^3, 8 Gaussian blobs, P = 12, mixed, tol 1e-9)
+    in the launch configuration the benchmark times (two FP32 steps per 3-D
+    blocked launch): the oracle's residual of the returned u is within
+    tolerance; at this size the blocked steps give the bits of single steps; and
+    one FP32 step agrees with the oracle within the rounding bound on sampled z
+    planes (first, last, and both sides of a 64-plane segment boundary)."""
+    n = 512
+    dims = (n, n, n)
+    f, u0 = W.gaussian_blobs_3d(n, 3)
+    plan = srj.Plan.from_table(dims, 12, "mixed")
+    assert plan.temporal_depth() == 2
+    fd = dev(f)
+    ud = dev(u0)
+    st = plan.solve(fd, ud, 1e-9, 200)
+    u = ud.cpu().numpy()
+    del ud
+    r0, _ = oracle.residual(dims, plan.h, f, u0)
+    l2, _ = oracle.residual(dims, plan.h, f, u)
+    assert l2 <= 1e-9 * r0 * (1 + 1e-9), (l2 / r0, st)
+    # blocked (depth 2) against single steps, from u0, even and ragged counts
+    for first, count in [(0, 8), (3, 7)]:
+        plan.set_temporal_depth(2)
+        got = dev(u0)
+        plan.steps(fd, got, first, count)
+        plan.set_temporal_depth(1)
+        ref = dev(u0)
+        plan.steps(fd, ref, first, count)
+        assert torch.equal(got, ref), (first, count)
+        del got, ref
+    plan.set_temporal_depth(2)
+    # one step of the largest weight on the converged field, against the oracle on z slabs
+    row = srj.schedules.lookup(3, n, 12)
+    k = int(np.argmax(row["omega"][row["order"]]))
+    w = row["omega"][row["order"][k]]
+    ud2 = dev(u)
+    plan.steps(fd, ud2, k, 1)
+    got = ud2.cpu().numpy()
+    del ud2
+    h = plan.h
+    c = w / 6
+    for z in (1, 2, 64, 65, 257, n - 1, n):
+        sl = slice(z - 1, z + 2)
+        u32 = np.ascontiguousarray(u[sl]).astype(np.float32).astype(np.float64)
+        f32 = (h * h * np.ascontiguousarray(f[sl])).astype(np.float32).astype(np.float64) / (h * h)
+        ref = oracle.sweep((n, n, 1), h, w, f32, u32)[1]
+        nb = sum(np.abs(np.roll(u32, s, axis=a)) for a in (0, 1, 2) for s in (-1, 1))[1]
+        bound = 8 * 2.0 ** -24 * (np.abs(u32[1]) + c * (nb + np.abs(h * h * f32[1]) + 6 * np.abs(u32[1])))
+        diff = np.abs(got[z] - ref)
+        assert np.all(diff[1:-1, 1:-1] <= bound[1:-1, 1:-1]), (z, float(diff[1:-1, 1:-1].max()))
+
+
 @pytest.mark.parametrize("dims", [(37, 23), (130, 67), (1, 1), (5, 300), (129, 129), (300, 5), (1000, 700)])
 def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
     """Temporal blocking (T steps per launch on register-resident tiles) must give

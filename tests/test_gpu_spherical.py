@@ -161,3 +161,29 @@ def test_spherical_temporal_depth_rules():
     p2 = sp.SphericalPlan((16, 16), row["omega"], row["q"], row["order"], precision="mixed")
     with pytest.raises(Exception):
         p2.set_temporal_depth(9)
+
+
+def test_bench_size_mixed_solve():
+    """The spherical benchmark problem at its size (Sect. 5.2 test, 1024^2,
+    P = 10, mixed, tol 1e-10) with the default blocked depth: the oracle's
+    residual of the returned field meets the tolerance, and the solve gives the
+    bits of the same solve with single-step launches."""
+    import srj_workloads as W
+    n = 1024
+    dims = (n, n)
+    b, u0 = W.spherical_problem_2d(n, 5)
+    row = sch.lookup(2, n, 10)
+    coef = sp.coefficients(dims)
+    plan = sp.SphericalPlan(dims, row["omega"], row["q"], row["order"], coef=coef, precision="mixed")
+    assert plan.temporal_depth() == 8
+    outs, stats = [], []
+    for T in (8, 1):
+        plan.set_temporal_depth(T)
+        ud = dev(u0)
+        stats.append(plan.solve(dev(b), ud, 1e-10, 400))
+        outs.append(ud.cpu().numpy())
+    assert stats[0]["cycles"] == stats[1]["cycles"]
+    assert np.array_equal(outs[0], outs[1])
+    r0, _ = oracle.sph_residual(dims, coef, b, u0)
+    l2, _ = oracle.sph_residual(dims, coef, b, outs[0])
+    assert l2 <= 1e-10 * r0 * (1 + 1e-9), (l2 / r0, stats[0])
