@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 3-D 512^3 and batched secondary measurements")
-    ap.add_argument("--kernel-case", choices=["f32", "f64", "sph", "sphmix"], default=None,
+    ap.add_argument("--kernel-case", choices=["f32", "f64", "sph", "sphmix", "batch"], default=None,
                     help="profiling aid: run --count sweeps of one precision on an --n x --n grid "
-                         "(plain Jacobi weight) through srj_steps and exit; prints no JSON")
+                         "(plain Jacobi weight) through srj_steps, or (batch) one untimed and one timed "
+                         "solve of the batched workload, and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
     ap.add_argument("--ndim", type=int, default=2, choices=[2, 3], help="kernel-case: grid dimension (n^ndim points)")
     ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
@@ -74,6 +75,10 @@ def run_kernel_case(args):
     n = args.n
     torch.cuda.set_device(0)
     dims = (n,) * args.ndim
+    if args.kernel_case == "batch":
+        res = batched_workload(torch.cuda.current_stream())
+        print("kernel case batch:", res)
+        return 0
     if args.kernel_case == "sphmix":  # one mixed-precision cycle of the Sect. 5.2 test (blocked FP32 sweeps)
         from paper_1511_04292_gb300 import spherical as sp
         b_h, u0_h = W.spherical_problem_2d(n, 5)
@@ -270,7 +275,18 @@ def secondary_workloads(stream):
         "sweep_kernel": "k_sweep_f64<2>"}
     del fa, ga, ta, ua, loss, aplan
     torch.cuda.empty_cache()
-    # batched: 256 problems, n in {64..1024}, P in 5..10, tol 1e-10
+    out.update(batched_workload(stream))
+    return out
+
+
+def batched_workload(stream):
+    """One timed solve of the batched workload: 256 problems, n in {64..1024},
+    P in 5..10, mixed precision, tol 1e-10 (after one untimed solve)."""
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    out = {}
     specs = W.batch_specs()
     probs, fs, u0s = [], [], []
     for nn, P, seed in specs:

@@ -3,19 +3,22 @@
 // times per M-cycle), solved together in mixed precision (FP32 cycles on the
 // defect equation inside FP64 correction, as in srj_solve).
 //
-// Work is organised in phases.  One phase is five launches:
-//   1. blocked FP32 sweep over the tiles of every active problem; each problem
-//      advances by n = min(T, M - k) steps of its own cycle order;
-//   2. advance: per problem, k += n, swap the correction buffers, flag the end
-//      of a cycle;
+// Work is organised in phases.  One phase is four launches:
+//   1. step (one thread per problem): the cycle-end test of the previous phase
+//      (norms, convergence test of the Sect. 4.1 monitor on b - A u, restart of
+//      the next cycle from e = 0), the problem's sweep record for this phase,
+//      and its state after the sweep (k += n with n = min(T, M - k), buffers
+//      swapped, cycle end flagged);
+//   2. blocked FP32 sweep over the tiles of every active problem;
 //   3. FP64 update u += e / s for the problems whose cycle ended;
 //   4. FP64 residual r = b - A u for them (written as FP32 r * s, with L2 / max
-//      partial sums per row block);
-//   5. finalize: per problem, norms, convergence test at the cycle end
-//      (Sect. 4.1 monitor on b - A u), restart of the next cycle from e = 0.
+//      partial sums per row block).
 // Kernel boundaries order the phases (no device-side waits); every launch reads
-// the per-problem state from device memory, so one CUDA graph of G phases is
-// captured at creation and replayed until no problem is active.
+// the per-problem state from device memory, so one CUDA graph of G phases (and
+// a closing cycle-end test) is captured and replayed until no problem is
+// active.  Every active problem swaps its buffers in every phase and all start
+// together, so with G even a problem's buffer index is the phase's parity in
+// the graph, a launch parameter of the grouped sweep.
 #include "srj_internal.h"
 #include "../../include/srj.h"
 
@@ -24,7 +27,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -55,13 +60,10 @@ constexpr int kPhasesPerGraph = 16;
 
 enum { kFinInit0 = 0, kFinInit1 = 1, kFinCycle = 2 };
 
-// Per-problem arguments of the coming sweep phase (0 steps when inactive).
-__global__ void k_batch_prepare(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
-                                const float* __restrict__ cw, srj::BatchArgs* __restrict__ args, int nprob, int T) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nprob) return;
-    const srj::BatchState s = st[p];
-    const srj::BatchProb P = probs[p];
+// The step record of problem p for the coming phase (0 steps when inactive),
+// then its state after that phase's sweep.
+__device__ __forceinline__ void prepare_and_advance(const srj::BatchProb& P, srj::BatchState& s, const float* cw,
+                                                    srj::BatchArgs* args, int T) {
     srj::BatchArgs a;
     a.n = s.active ? min(T, P.M - s.k) : 0;
     a.ein = s.cur ? P.eb : P.ea;
@@ -73,27 +75,65 @@ __global__ void k_batch_prepare(const srj::BatchProb* __restrict__ probs, const 
     a.fresh = s.fresh;
 #pragma unroll
     for (int t = 0; t < 8; ++t) a.c[t] = (t < a.n) ? cw[P.c_off + s.k + t] : 0.f;
-    args[p] = a;
+    args[P.rec] = a;
+    if (!s.active) return;
+    s.k += a.n;
+    s.cur ^= 1;
+    s.fresh = 0;
+    if (s.k == P.M) s.cycle_end = 1;
 }
 
-__global__ void k_batch_advance(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st, int nprob,
-                                int T) {
+// L2^2 and max of the residual from the problem's row-block partials (in row order).
+__device__ __forceinline__ void sum_partials(const srj::BatchProb& P, const double* partials, double& a, double& m) {
+    a = 0.0;
+    m = 0.0;
+    for (int b = P.rb_begin; b < P.rb_end; ++b) {
+        a += partials[2 * b];
+        m = fmax(m, partials[2 * b + 1]);
+    }
+}
+
+// Cycle-end test (Sect. 4.1 monitor on b - A u at the end of a cycle):
+// converged, diverged, out of cycles, stagnated at the floating-point floor, or
+// the next cycle starts from e = 0.
+__device__ __forceinline__ void finish_cycle(const srj::BatchProb& P, srj::BatchState& s, const double* partials,
+                                             double tol, int max_cycles) {
+    double a, m;
+    sum_partials(P, partials, a, m);
+    const double l2 = sqrt(a);
+    s.l2 = l2;
+    s.linf = (a == a) ? m : a;
+    s.cycles += 1;
+    s.cycle_end = 0;
+    if (!isfinite(l2) || l2 > 1e6 * s.r0) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
+    else if (l2 / s.r0 <= tol) { s.status = SRJ_OK; s.active = 0; }
+    else if (s.cycles >= max_cycles) { s.status = SRJ_ERR_NOT_CONVERGED; s.active = 0; }
+    else if (!(l2 < 0.5 * s.best) && ++s.stall >= 4) {  // floating-point floor reached
+        s.status = SRJ_ERR_NOT_CONVERGED; s.stagnated = 1; s.active = 0;
+    } else {
+        if (l2 < 0.5 * s.best) { s.best = l2; s.stall = 0; }
+        s.k = 0; s.fresh = 1;
+    }
+}
+
+__global__ void k_batch_step(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st,
+                             const double* __restrict__ partials, const float* __restrict__ cw,
+                             srj::BatchArgs* __restrict__ args, int nprob, int T, double tol, int max_cycles) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nprob) return;
     srj::BatchState s = st[p];
-    if (!s.active) return;
-    const int n = min(T, probs[p].M - s.k);
-    s.k += n;
-    s.cur ^= 1;
-    s.fresh = 0;
-    if (s.k == probs[p].M) s.cycle_end = 1;
+    const srj::BatchProb P = probs[p];
+    if (s.active && s.cycle_end) finish_cycle(P, s, partials, tol, max_cycles);
+    prepare_and_advance(P, s, cw, args, T);
     st[p] = s;
 }
 
 // u += inv_scale * e on the rows of one row block, for problems at a cycle end.
+// Block b takes row block ids[b] (b itself when ids is NULL).
 __global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
-                               const int2* __restrict__ rowblocks) {
-    const int2 rb = rowblocks[blockIdx.x];
+                               const int2* __restrict__ rowblocks, const int* __restrict__ ids) {
+    const int id = ids ? ids[blockIdx.x] : (int)blockIdx.x;
+    const int2 rb = rowblocks[id];
     const srj::BatchState s = st[rb.x];
     if (!s.active || !s.cycle_end) return;
     const srj::BatchProb P = probs[rb.x];
@@ -107,12 +147,15 @@ __global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const s
 
 // r = (h^2 f + sum nbrs u) - 4 u in the oracle's operation order; optional FP32
 // defect r * scale; per-block L2 / max partials.  `all`: every active problem
-// (initial residual), otherwise only problems at a cycle end.
+// (initial residual), otherwise only problems at a cycle end.  Block b takes
+// row block ids[b] (b itself when ids is NULL); its partials go to that row
+// block's slot.
 __global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
-                                 const int2* __restrict__ rowblocks, double* __restrict__ partials, int write_r32,
-                                 int all) {
+                                 const int2* __restrict__ rowblocks, const int* __restrict__ ids,
+                                 double* __restrict__ partials, int write_r32, int all) {
     __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
-    const int2 rb = rowblocks[blockIdx.x];
+    const int id = ids ? ids[blockIdx.x] : (int)blockIdx.x;
+    const int2 rb = rowblocks[id];
     const srj::BatchState s = st[rb.x];
     const bool work = s.active && (all || s.cycle_end);
     double ss = 0.0, mx = 0.0;
@@ -146,8 +189,8 @@ __global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const
     if (threadIdx.x == 0) {
         double a = 0.0, m = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += sh_ss[i]; m = fmax(m, sh_mx[i]); }
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = (a == a) ? m : a;
+        partials[2 * id] = a;
+        partials[2 * id + 1] = (a == a) ? m : a;
     }
 }
 
@@ -159,50 +202,43 @@ __global__ void k_batch_finalize(const srj::BatchProb* __restrict__ probs, srj::
     srj::BatchState s = st[p];
     if (!s.active) return;
     if (mode == kFinInit1) { s.cycle_end = 0; s.fresh = 1; s.k = 0; st[p] = s; return; }
-    if (mode == kFinCycle && !s.cycle_end) return;
-    double a = 0.0, m = 0.0;
-    for (int b = probs[p].rb_begin; b < probs[p].rb_end; ++b) {
-        a += partials[2 * b];
-        m = fmax(m, partials[2 * b + 1]);
-    }
-    const double l2 = sqrt(a);
-    s.l2 = l2;
-    s.linf = (a == a) ? m : a;
-    if (mode == kFinInit0) {
-        s.r0 = l2;
-        s.best = l2;
-        s.stall = 0;
-        if (!isfinite(l2)) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
-        else if (l2 == 0.0 || !(tol < 1.0)) { s.status = SRJ_OK; s.active = 0; }
-        else {
-            int ex = 0;
-            frexp(s.linf, &ex);
-            s.scale = ldexp(1.0, -ex);
-            s.inv_scale = ldexp(1.0, ex);
-        }
+    if (mode == kFinCycle) {
+        if (!s.cycle_end) return;
+        finish_cycle(probs[p], s, partials, tol, max_cycles);
         st[p] = s;
         return;
     }
-    s.cycles += 1;
-    s.cycle_end = 0;
-    if (!isfinite(l2) || l2 > 1e6 * s.r0) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
-    else if (l2 / s.r0 <= tol) { s.status = SRJ_OK; s.active = 0; }
-    else if (s.cycles >= max_cycles) { s.status = SRJ_ERR_NOT_CONVERGED; s.active = 0; }
-    else if (!(l2 < 0.5 * s.best) && ++s.stall >= 4) {  // floating-point floor reached
-        s.status = SRJ_ERR_NOT_CONVERGED; s.stagnated = 1; s.active = 0;
-    } else {
-        if (l2 < 0.5 * s.best) { s.best = l2; s.stall = 0; }
-        s.k = 0; s.fresh = 1;
+    double a, m;  // kFinInit0: the initial residual
+    sum_partials(probs[p], partials, a, m);
+    const double l2 = sqrt(a);
+    s.l2 = l2;
+    s.linf = (a == a) ? m : a;
+    s.r0 = l2;
+    s.best = l2;
+    s.stall = 0;
+    if (!isfinite(l2)) { s.status = SRJ_ERR_DIVERGED; s.active = 0; }
+    else if (l2 == 0.0 || !(tol < 1.0)) { s.status = SRJ_OK; s.active = 0; }
+    else {
+        int ex = 0;
+        frexp(s.linf, &ex);
+        s.scale = ldexp(1.0, -ex);
+        s.inv_scale = ldexp(1.0, ex);
     }
     st[p] = s;
 }
 
-__global__ void k_batch_count(const srj::BatchState* __restrict__ st, int nprob, int* __restrict__ out) {
+// Number of problems still iterating, and their flags.
+__global__ void k_batch_count(const srj::BatchState* __restrict__ st, int nprob, int* __restrict__ out,
+                              unsigned char* __restrict__ flags) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     int c = 0;
-    for (int p = threadIdx.x; p < nprob; p += blockDim.x) c += st[p].active ? 1 : 0;
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+        const int a = st[p].active ? 1 : 0;
+        flags[p] = (unsigned char)a;
+        c += a;
+    }
     atomicAdd(&cnt, c);
     __syncthreads();
     if (threadIdx.x == 0) *out = cnt;
@@ -218,6 +254,17 @@ struct srj_batch {
     std::vector<int> M;
     int64_t total_points = 0;
     int ntiles = 0, nrowblocks = 0;
+    bool grouped = false;       // at most kMaxBatchGroups grid sizes: grouped sweep
+    srj::BatchGroups groups{};  // every problem launched
+    std::vector<int> gid, gz;   // group and group-local index of each problem
+    std::vector<int4> tiles;    // tile list (problem, tile x, tile y) of every problem
+    std::vector<int> tile_begin;  // first tile of each problem in `tiles`
+    std::vector<unsigned char> launched;  // problems the graph's launches cover
+    cudaGraph_t graph = nullptr;          // kept: its nodes are re-targeted between launches
+    std::vector<cudaGraphNode_t> sweep_nodes, rowblock_nodes;
+    int* d_rb_ids = nullptr;              // row blocks of the launched problems
+    unsigned char* d_flags = nullptr;
+    unsigned char* h_flags = nullptr;
     srj::BatchProb* d_probs = nullptr;
     srj::BatchState* d_state = nullptr;
     int4* d_tiles = nullptr;
@@ -236,6 +283,9 @@ struct srj_batch {
 
     ~srj_batch() {
         if (phases) cudaGraphExecDestroy(phases);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(d_rb_ids); cudaFree(d_flags);
+        if (h_flags) cudaFreeHost(h_flags);
         if (cap) cudaStreamDestroy(cap);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -247,31 +297,118 @@ struct srj_batch {
 
 namespace {
 
-cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles) {
-    const int pb = (b->nprob + kThreads - 1) / kThreads;
-    k_batch_prepare<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_cw, b->d_args, b->nprob, b->T);
-    cudaError_t e = srj::launch_batch_sweep_tb(b->T, (unsigned)b->ntiles, b->d_tiles, b->d_args, s);
+// The node a capture has just added (the only dependency of what comes next).
+cudaError_t last_node(cudaStream_t s, cudaGraphNode_t* out) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
     if (e != cudaSuccess) return e;
-    k_batch_advance<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->nprob, b->T);
-    k_batch_update<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks);
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 1, 0);
-    k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinCycle, tol,
-                                             max_cycles);
+    if (st != cudaStreamCaptureStatusActive || nd != 1) return cudaErrorStreamCaptureInvalidated;
+    *out = deps[0];
+    return cudaSuccess;
+}
+
+cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles, int parity) {
+    const int pb = (b->nprob + kThreads - 1) / kThreads;
+    k_batch_step<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->d_cw, b->d_args, b->nprob, b->T,
+                                         tol, max_cycles);
+    cudaError_t e = b->grouped
+                        ? srj::launch_batch_sweep_grouped(b->T, (unsigned)b->ntiles, b->groups, b->d_pool, b->d_args,
+                                                          parity, s)
+                        : srj::launch_batch_sweep_tb(b->T, (unsigned)b->ntiles, b->d_tiles, b->d_args, s);
+    cudaGraphNode_t n;
+    if (e == cudaSuccess) e = last_node(s, &n);
+    if (e != cudaSuccess) return e;
+    b->sweep_nodes.push_back(n);
+    k_batch_update<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_rb_ids);
+    e = last_node(s, &n);
+    if (e != cudaSuccess) return e;
+    b->rowblock_nodes.push_back(n);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_rb_ids,
+                                                        b->d_partials, 1, 0);
+    e = last_node(s, &n);
+    if (e != cudaSuccess) return e;
+    b->rowblock_nodes.push_back(n);
     return cudaGetLastError();
 }
 
-int capture_phases(srj_batch* b, double tol, int max_cycles) {
+// Point the graph's sweep, update and residual launches at the problems flagged
+// in `want` (those still iterating at the start of the next graph launch).
+// Problems that finish during a launch keep their blocks until the next one;
+// those blocks see no steps and no cycle end and leave early.
+int retarget(srj_batch* b, const unsigned char* want, cudaStream_t s) {
+    if (b->launched.size() == (size_t)b->nprob && std::equal(b->launched.begin(), b->launched.end(), want)) return SRJ_OK;
+    std::vector<int> ids;
+    unsigned ntiles = 0;
+    srj::BatchGroups G = b->groups;
+    std::vector<int4> tl;
+    if (b->grouped) {
+        std::vector<std::vector<int>> mem(G.ngroups);
+        for (int p = 0; p < b->nprob; ++p)
+            if (want[p]) mem[b->gid[p]].push_back(b->gz[p]);
+        int mb = 0, tb = 0;
+        for (int g = 0; g < G.ngroups; ++g) {
+            G.mbase[g] = mb;
+            G.tile_begin[g] = tb;
+            for (int m : mem[g]) G.member[mb++] = (uint16_t)m;
+            tb += (int)mem[g].size() * G.gx[g] * G.gy[g];
+        }
+        G.tile_begin[G.ngroups] = tb;
+        ntiles = (unsigned)tb;
+    } else {
+        for (int p = 0; p < b->nprob; ++p)
+            if (want[p]) tl.insert(tl.end(), b->tiles.begin() + b->tile_begin[p], b->tiles.begin() + b->tile_begin[p + 1]);
+        ntiles = (unsigned)tl.size();
+    }
+    for (int p = 0; p < b->nprob; ++p)
+        if (want[p])
+            for (int r = b->probs[p].rb_begin; r < b->probs[p].rb_end; ++r) ids.push_back(r);
+    if (ntiles == 0 || ids.empty()) return SRJ_OK;  // nothing left to launch: the solve loop ends
+    SRJ_BCUDA(cudaMemcpyAsync(b->d_rb_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
+    if (!b->grouped)
+        SRJ_BCUDA(cudaMemcpyAsync(b->d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, s));
+    for (cudaGraphNode_t n : b->sweep_nodes)
+        SRJ_BCUDA(srj::batch_sweep_set_node(b->phases, n, ntiles, b->grouped ? &G : nullptr));
+    for (cudaGraphNode_t n : b->rowblock_nodes) {
+        cudaKernelNodeParams kp{};
+        SRJ_BCUDA(cudaGraphKernelNodeGetParams(n, &kp));
+        kp.gridDim = dim3((unsigned)ids.size(), 1, 1);
+        SRJ_BCUDA(cudaGraphExecKernelNodeSetParams(b->phases, n, &kp));
+    }
+    b->launched.assign(want, want + b->nprob);
+    return SRJ_OK;
+}
+
+int capture_phases(srj_batch* b, double tol, int max_cycles, cudaStream_t s) {
     if (b->phases) { cudaGraphExecDestroy(b->phases); b->phases = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->sweep_nodes.clear();
+    b->rowblock_nodes.clear();
+    b->launched.clear();
+    // the captured launches cover every problem: identity row-block list and full tile list
+    std::vector<int> ids(b->nrowblocks);
+    for (int i = 0; i < b->nrowblocks; ++i) ids[i] = i;
+    SRJ_BCUDA(cudaMemcpyAsync(b->d_rb_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
+    SRJ_BCUDA(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(), cudaMemcpyHostToDevice, s));
     cudaGraph_t graph = nullptr;
     SRJ_BCUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
-    for (int i = 0; i < kPhasesPerGraph && err == cudaSuccess; ++i) err = issue_phase(b, b->cap, tol, max_cycles);
+    static_assert(kPhasesPerGraph % 2 == 0, "buffer parity must repeat from one graph launch to the next");
+    for (int i = 0; i < kPhasesPerGraph && err == cudaSuccess; ++i) err = issue_phase(b, b->cap, tol, max_cycles, i & 1);
+    if (err == cudaSuccess) {  // cycle-end test of the last phase, so that the state is final between launches
+        const int pb = (b->nprob + kThreads - 1) / kThreads;
+        k_batch_finalize<<<pb, kThreads, 0, b->cap>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinCycle, tol,
+                                                      max_cycles);
+        err = cudaGetLastError();
+    }
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); SRJ_BCUDA(err); }
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); b->sweep_nodes.clear(); b->rowblock_nodes.clear(); SRJ_BCUDA(err); }
     SRJ_BCUDA(e2);
     cudaError_t e3 = cudaGraphInstantiate(&b->phases, graph, 0);
-    cudaGraphDestroy(graph);
-    SRJ_BCUDA(e3);
+    if (e3 != cudaSuccess) { cudaGraphDestroy(graph); b->sweep_nodes.clear(); b->rowblock_nodes.clear(); SRJ_BCUDA(e3); }
+    b->graph = graph;
+    b->launched.assign(b->nprob, 1);
     b->graph_tol = tol;
     b->graph_max_cycles = max_cycles;
     return SRJ_OK;
@@ -297,6 +434,48 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
     b->T = temporal_depth;
     int TX = 0, TY = 0;
     srj::tb_tile_shape(b->T, &TX, &TY);
+
+    // Grid sizes: with at most kMaxBatchGroups distinct ones the pool is laid out
+    // group by group and the grouped sweep is used (BatchGroups).
+    std::vector<int> gid(nprob, 0), gz(nprob, 0);
+    std::vector<std::pair<int64_t, int64_t>> gdims;
+    std::vector<int> gcount;
+    {
+        std::map<std::pair<int64_t, int64_t>, int> seen;
+        bool dims_ok = true;
+        for (int p = 0; p < nprob; ++p) {
+            const std::pair<int64_t, int64_t> d(pr[p].nx, pr[p].ny);
+            if (d.first < 1 || d.second < 1 || d.first > 65536 || d.second > 65536) dims_ok = false;
+            auto it = seen.find(d);
+            int g = 0;
+            if (it == seen.end()) {
+                g = (int)gdims.size();
+                seen.emplace(d, g);
+                gdims.push_back(d);
+                gcount.push_back(0);
+            } else {
+                g = it->second;
+            }
+            gid[p] = g;
+            gz[p] = gcount[g]++;
+        }
+        b->grouped = dims_ok && gdims.size() <= (size_t)srj::kMaxBatchGroups && nprob <= srj::kMaxGroupedProblems;
+    }
+    const int ngroups = (int)gdims.size();
+    std::vector<size_t> goff, gn32;
+    std::vector<int> grec;
+    size_t grouped_floats = 0;
+    if (b->grouped) {
+        int racc = 0;
+        for (int g = 0; g < ngroups; ++g) {
+            const int64_t dims[2] = {gdims[g].first, gdims[g].second};
+            gn32.push_back((size_t)((srj::make_geom(2, dims).n32 + 63) / 64 * 64));
+            goff.push_back(grouped_floats);
+            grouped_floats += (size_t)gcount[g] * 3 * gn32[g];
+            grec.push_back(racc);
+            racc += gcount[g];
+        }
+    }
 
     std::vector<float> cw;
     std::vector<int4> tiles;
@@ -345,11 +524,18 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
         P.c_off = (int)cw.size();
         for (int32_t v : order) cw.push_back((float)(w[v] / 4.0));
         const size_t n32 = (size_t)((geo.n32 + 63) / 64 * 64);
-        pool_off.push_back(pool_floats);
-        pool_floats += 3 * n32;
+        if (b->grouped) {
+            pool_off.push_back(goff[gid[p]] + (size_t)gz[p] * 3 * gn32[gid[p]]);
+            P.rec = grec[gid[p]] + gz[p];
+        } else {
+            pool_off.push_back(pool_floats);
+            pool_floats += 3 * n32;
+            P.rec = p;
+        }
         b->M.push_back((int)M);
         b->total_points += q.nx * q.ny;
         const int gx = (int)((q.nx + TX - 1) / TX), gy = (int)((q.ny + TY - 1) / TY);
+        b->tile_begin.push_back((int)tiles.size());
         for (int by = 0; by < gy; ++by)
             for (int bx = 0; bx < gx; ++bx) tiles.push_back(make_int4(p, bx, by, 0));
         P.rb_begin = (int)rowblocks.size();
@@ -357,8 +543,41 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
         P.rb_end = (int)rowblocks.size();
         if (cw.size() > (size_t)1 << 30) return bail(bfail(SRJ_ERR_INVALID_ARG, "weight table too large"));
     }
+    if (tiles.size() > (size_t)INT32_MAX || rowblocks.size() > (size_t)INT32_MAX)
+        return bail(bfail(SRJ_ERR_INVALID_ARG, "too many tiles"));
+    b->tile_begin.push_back((int)tiles.size());
+    b->tiles = tiles;
+    b->gid = gid;
+    b->gz = gz;
     b->ntiles = (int)tiles.size();
     b->nrowblocks = (int)rowblocks.size();
+    if (b->grouped) {
+        pool_floats = grouped_floats;
+        srj::BatchGroups& G = b->groups;
+        G.ngroups = ngroups;
+        int64_t tb = 0;
+        for (int g = 0; g < ngroups; ++g) {
+            const int64_t dims[2] = {gdims[g].first, gdims[g].second};
+            const srj::Geom geo = srj::make_geom(2, dims);
+            G.tile_begin[g] = (int)tb;
+            G.gx[g] = (int)((dims[0] + TX - 1) / TX);
+            G.gy[g] = (int)((dims[1] + TY - 1) / TY);
+            tb += (int64_t)gcount[g] * G.gx[g] * G.gy[g];
+            G.nx[g] = (int)dims[0];
+            G.ny[g] = (int)dims[1];
+            G.rec[g] = grec[g];
+            G.p32[g] = geo.p32;
+            G.n32[g] = (int64_t)gn32[g];
+            G.off[g] = (int64_t)goff[g];
+        }
+        G.tile_begin[ngroups] = (int)tb;
+        int mb = 0;
+        for (int g = 0; g < ngroups; ++g) {
+            G.mbase[g] = mb;
+            for (int m = 0; m < gcount[g]; ++m) G.member[mb++] = (uint16_t)m;
+        }
+        if (tb != b->ntiles) return bail(bfail(SRJ_ERR_INVALID_ARG, "internal: grouped tile count %lld != %d", (long long)tb, b->ntiles));
+    }
     if (cudaGetDevice(&b->device) != cudaSuccess) return bail(bfail(SRJ_ERR_CUDA, "no CUDA device"));
     auto alloc = [](void** ptr, size_t by) { return cudaMalloc(ptr, by) == cudaSuccess; };
     bool ok = alloc((void**)&b->d_pool, sizeof(float) * pool_floats) &&
@@ -369,7 +588,9 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
               alloc((void**)&b->d_rowblocks, sizeof(int2) * rowblocks.size()) &&
               alloc((void**)&b->d_cw, sizeof(float) * cw.size()) &&
               alloc((void**)&b->d_partials, sizeof(double) * 2 * rowblocks.size()) &&
-              alloc((void**)&b->d_count, sizeof(int));
+              alloc((void**)&b->d_count, sizeof(int)) &&
+              alloc((void**)&b->d_rb_ids, sizeof(int) * rowblocks.size()) &&
+              alloc((void**)&b->d_flags, (size_t)nprob);
     if (!ok) { cudaGetLastError(); return bail(bfail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
     for (int p = 0; p < nprob; ++p) {
         const int64_t dims[2] = {pr[p].nx, pr[p].ny};
@@ -385,6 +606,7 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
         cudaMemcpy(b->d_rowblocks, rowblocks.data(), sizeof(int2) * rowblocks.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_cw, cw.data(), sizeof(float) * cw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMallocHost((void**)&b->h_count, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_flags, (size_t)nprob) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
         srj::tb_prepare() != cudaSuccess) {
@@ -438,13 +660,19 @@ int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, dou
     const int pb = (b->nprob + kThreads - 1) / kThreads;
     const int mc = (int)std::max<int64_t>(max_cycles, 1);
     // initial residual (norms, then the scaled FP32 defect)
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 0, 1);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, b->d_partials,
+                                                        0, 1);
     k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit0, tol, mc);
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_partials, 1, 1);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, b->d_partials,
+                                                        1, 1);
     k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit1, tol, mc);
     SRJ_BCUDA(cudaGetLastError());
-    if (b->graph_tol != tol || b->graph_max_cycles != mc) {
-        int rc = capture_phases(b, tol, mc);
+    if (b->graph_tol != tol || b->graph_max_cycles != mc || !b->phases) {
+        int rc = capture_phases(b, tol, mc, s);
+        if (rc) return rc;
+    } else {
+        const std::vector<unsigned char> all(b->nprob, 1);
+        int rc = retarget(b, all.data(), s);  // a previous solve may have left fewer problems launched
         if (rc) return rc;
     }
     // Each phase advances every active problem by at least one step, so
@@ -458,10 +686,13 @@ int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, dou
         for (;;) {
             SRJ_BCUDA(cudaGraphLaunch(b->phases, s));
             phases += kPhasesPerGraph;
-            k_batch_count<<<1, kThreads, 0, s>>>(b->d_state, b->nprob, b->d_count);
+            k_batch_count<<<1, kThreads, 0, s>>>(b->d_state, b->nprob, b->d_count, b->d_flags);
             SRJ_BCUDA(cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SRJ_BCUDA(cudaMemcpyAsync(b->h_flags, b->d_flags, (size_t)b->nprob, cudaMemcpyDeviceToHost, s));
             SRJ_BCUDA(cudaStreamSynchronize(s));
             if (*b->h_count == 0 || phases >= max_phases) break;
+            int rc = retarget(b, b->h_flags, s);  // drop the problems that have finished
+            if (rc) return rc;
         }
     }
     SRJ_BCUDA(cudaEventRecord(b->ev1, s));

@@ -111,6 +111,7 @@ struct BatchProb {
     const double* f;       // caller's arrays (set per solve)
     double* u;
     int rb_begin, rb_end;  // range of the problem's row blocks (residual partials)
+    int rec;               // index of the problem's sweep record (BatchArgs)
 };
 
 // Dynamic per-problem state, in device memory.
@@ -129,8 +130,9 @@ struct BatchState {
     int stagnated, pad2;
 };
 
-// What one sweep phase needs of a problem, written by k_batch_prepare at the
-// start of the phase so that a sweep block reads one record after its tile.
+// What one sweep phase needs of a problem, written at the start of the phase.
+// The tile-list sweep reads every field; the grouped sweep (BatchGroups) takes
+// the workspaces from its launch parameters and reads n, fresh and c.
 struct BatchArgs {
     const float* ein;      // current correction
     float* eout;           // next correction
@@ -142,8 +144,38 @@ struct BatchArgs {
     float c[8];            // weight / 4 of each step
 };
 
+// Problems of one grid size form a group; a group's FP32 workspaces follow each
+// other in the pool at a fixed stride (ea, eb, r32 of n32 floats each per
+// problem) and its problems have consecutive record indices.  A sweep block
+// then finds its problem, tile and workspaces from these launch parameters
+// alone, without a memory read ahead of its tile loads.
+// Only the problems still iterating are launched: member[] lists, per group,
+// the group-local indices of the launched problems (the z-th launched problem
+// of group g is member[mbase[g] + z]).
+constexpr int kMaxBatchGroups = 16;
+constexpr int kMaxGroupedProblems = 1024;
+struct BatchGroups {
+    int ngroups;
+    int tile_begin[kMaxBatchGroups + 1];  // first block of each group in launch order
+    int gx[kMaxBatchGroups], gy[kMaxBatchGroups];  // tiles per problem in x / y
+    int nx[kMaxBatchGroups], ny[kMaxBatchGroups];  // interior points
+    int rec[kMaxBatchGroups];                      // record index of the group's first problem
+    int mbase[kMaxBatchGroups];                    // first entry of the group in member[]
+    int64_t p32[kMaxBatchGroups];                  // float32 row pitch
+    int64_t n32[kMaxBatchGroups];                  // floats per workspace
+    int64_t off[kMaxBatchGroups];                  // pool offset of the group's first problem
+    uint16_t member[kMaxGroupedProblems];
+};
+
 void tb_tile_shape(int T, int* TX, int* TY);
 cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const int4* tiles, const BatchArgs* args, cudaStream_t s);
+// parity: the phase's position in its graph modulo 2, which is every active
+// problem's buffer index (0: input in ea, output in eb; 1: the reverse).
+cudaError_t launch_batch_sweep_grouped(int T, unsigned ntiles, const BatchGroups& G, float* pool,
+                                       const BatchArgs* args, int parity, cudaStream_t s);
+// Relaunch shape of a captured batch sweep node (either kind): ntiles blocks
+// and, for the grouped sweep, the launched problems in G.
+cudaError_t batch_sweep_set_node(cudaGraphExec_t exec, cudaGraphNode_t node, unsigned ntiles, const BatchGroups* G);
 
 // Host-side schedule helpers shared by the plan and the batch (srj_plan.cu).
 std::vector<int32_t> host_drift_order(const std::vector<double>& w, const std::vector<int32_t>& q, double kmin);

@@ -27,7 +27,6 @@ constexpr int kSX = 128;  // tile columns (floats)
 constexpr int kSY = 64;   // tile rows
 constexpr int kWarps = 8;
 constexpr int kBand = kSY / kWarps;
-constexpr unsigned kTileBytes = kSX * kSY * sizeof(float);
 
 // One warp's band of kBand rows lives in registers for all T steps: e[i]
 // (float4, 4 consecutive columns per lane) and the defect rr[i].  Only the
@@ -449,6 +448,129 @@ k_batch_sweep_tb(const int4* __restrict__ tiles, const BatchArgs* __restrict__ a
     }
 }
 
+// Batched sweep over problems grouped by grid size (BatchGroups): a block
+// derives its problem, tile and workspaces from the launch parameters, so its
+// loads of e and of the defect issue at once, and the problem's record of this
+// phase (steps, zero start, weights) is read alongside them.  Reading the
+// record first, as k_batch_sweep_tb does, puts a dependent load ahead of every
+// tile; on full-grid tiles that cost about a fifth of the sweep time.  The
+// input correction is read even at a cycle start (zero start) and then
+// replaced by zeros, which is what the tile-list kernel computes.
+template <int T>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_batch_sweep_grp(const BatchGroups G, float* __restrict__ pool, const BatchArgs* __restrict__ args, int parity) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int TX = kSX - 2 * HX, TY = kSY - 2 * T;
+    __shared__ float4 xch[2 * 2 * kWarps * 32];
+    __shared__ float csh[8];
+    const int bid = (int)blockIdx.x;
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < G.ngroups && bid >= G.tile_begin[g + 1]) ++g;
+    const int gx = G.gx[g];
+    const int local = bid - G.tile_begin[g];
+    const int tpp = gx * G.gy[g];
+    const int z = local / tpp;
+    const int rem = local - z * tpp;
+    const int by = rem / gx, bx = rem - by * gx;
+    const int nx = G.nx[g], ny = G.ny[g];
+    const int64_t p32 = G.p32[g], n32 = G.n32[g];
+    const int m = G.member[G.mbase[g] + z];
+    float* const wbase = pool + G.off[g] + (int64_t)m * 3 * n32;
+    const float* ein = wbase + (parity ? n32 : 0);
+    float* eout = wbase + (parity ? 0 : n32);
+    const float* rin = wbase + 2 * n32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
+    const int Yw = Y0 + w * kBand;
+    const bool xin = X0 >= 1 && X0 + kSX - 1 <= nx;
+    const bool yin = Y0 >= 1 && Y0 + kSY - 1 <= ny;
+    const int64_t base = (int64_t)Yw * p32 + X0 + 3 + 4 * lane;
+    float4 e[kBand], rr[kBand];
+    bool iny[kBand];
+    if (xin && yin) {
+        const float4* pe = reinterpret_cast<const float4*>(ein + base);
+        const float4* pr = reinterpret_cast<const float4*>(rin + base);
+        const int64_t stride = p32 / 4;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            e[i] = __ldg(pe + i * stride);
+            rr[i] = __ldg(pr + i * stride);
+            iny[i] = true;
+        }
+    } else {
+        const int col = X0 + 3 + 4 * lane;
+        const bool colok = col >= 0 && col + 4 <= p32;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int64_t y = (int64_t)Yw + i;
+            e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            rr[i] = e[i];
+            if (colok && y >= 0 && y < (int64_t)ny + 2) {
+                const int64_t off = y * p32 + col;
+                e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
+                rr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
+            }
+            iny[i] = y >= 1 && y <= ny;
+        }
+    }
+    const BatchArgs* __restrict__ Ap = args + G.rec[g] + m;
+    const int n = Ap->n;
+    const int fresh = Ap->fresh;
+    if (threadIdx.x < 8) csh[threadIdx.x] = Ap->c[threadIdx.x];
+    if (n == 0) return;  // problem no longer iterating (uniform over the block)
+    if (fresh) {
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    bool inx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int x = X0 + 4 * lane + j;
+        inx[j] = x >= 1 && x <= nx;
+    }
+    __syncthreads();  // the weights in csh
+    if (xin && yin) {
+        if (n == T) band_steps<T, false, false>(e, rr, xch, csh, T, lane, w, inx, iny);
+        else        band_steps<T, false, false>(e, rr, xch, csh, n, lane, w, inx, iny);
+    } else if (xin) {
+        band_steps<T, true, false>(e, rr, xch, csh, n, lane, w, inx, iny);
+    } else if (yin) {
+        band_steps<T, false, true>(e, rr, xch, csh, n, lane, w, inx, iny);
+    } else {
+        band_steps<T, true, true>(e, rr, xch, csh, n, lane, w, inx, iny);
+    }
+    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
+    if (lane < lane_lo || lane >= lane_hi) return;
+    if (xin && yin) {
+        float4* po = reinterpret_cast<float4*>(eout + base);
+        const int64_t stride = p32 / 4;
+#pragma unroll
+        for (int i = 0; i < kBand; ++i) {
+            const int row = w * kBand + i;
+            if (row >= T && row < T + TY) po[i * stride] = e[i];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kBand; ++i) {
+        const int row = w * kBand + i;
+        if (row < T || row >= T + TY) continue;
+        const int y = Y0 + row;
+        if (y < 1 || y > ny) continue;
+        const int x = X0 + 4 * lane;
+        float* dst = eout + (int64_t)y * p32 + x + 3;
+        if (inx[0] && inx[3]) {
+            *reinterpret_cast<float4*>(dst) = e[i];
+        } else {
+            if (inx[0]) dst[0] = e[i].x;
+            if (inx[1]) dst[1] = e[i].y;
+            if (inx[2]) dst[2] = e[i].z;
+            if (inx[3]) dst[3] = e[i].w;
+        }
+    }
+}
+
 size_t smem_bytes() { return 0; }
 
 }  // namespace
@@ -492,6 +614,12 @@ void launch_W(int T, dim3 grd, cudaStream_t s, const float* ein, const float* ri
 template <int T>
 void launch_batch_T(unsigned ntiles, cudaStream_t s, const int4* tiles, const BatchArgs* args) {
     k_batch_sweep_tb<T><<<ntiles, kWarps * 32, 0, s>>>(tiles, args);
+}
+
+template <int T>
+void launch_batch_grp_T(unsigned ntiles, cudaStream_t s, const BatchGroups& G, float* pool, const BatchArgs* args,
+                        int parity) {
+    k_batch_sweep_grp<T><<<ntiles, kWarps * 32, 0, s>>>(G, pool, args, parity);
 }
 
 cudaError_t tb_prepare() {
@@ -544,6 +672,37 @@ void tb_tile_shape(int T, int* TX, int* TY) {
     const int HX = T <= 4 ? 4 : 8;
     *TX = kSX - 2 * HX;
     *TY = kSY - 2 * T;
+}
+
+cudaError_t launch_batch_sweep_grouped(int T, unsigned ntiles, const BatchGroups& G, float* pool,
+                                       const BatchArgs* args, int parity, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    if (G.ngroups < 1 || G.ngroups > kMaxBatchGroups || G.tile_begin[G.ngroups] != (int)ntiles)
+        return cudaErrorInvalidValue;
+    switch (T) {
+        case 1: launch_batch_grp_T<1>(ntiles, s, G, pool, args, parity); break;
+        case 2: launch_batch_grp_T<2>(ntiles, s, G, pool, args, parity); break;
+        case 3: launch_batch_grp_T<3>(ntiles, s, G, pool, args, parity); break;
+        case 4: launch_batch_grp_T<4>(ntiles, s, G, pool, args, parity); break;
+        case 5: launch_batch_grp_T<5>(ntiles, s, G, pool, args, parity); break;
+        case 6: launch_batch_grp_T<6>(ntiles, s, G, pool, args, parity); break;
+        case 7: launch_batch_grp_T<7>(ntiles, s, G, pool, args, parity); break;
+        default: launch_batch_grp_T<8>(ntiles, s, G, pool, args, parity); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_sweep_set_node(cudaGraphExec_t exec, cudaGraphNode_t node, unsigned ntiles, const BatchGroups* G) {
+    if (ntiles == 0) return cudaErrorInvalidValue;
+    cudaKernelNodeParams p{};
+    cudaError_t e = cudaGraphKernelNodeGetParams(node, &p);
+    if (e != cudaSuccess) return e;
+    p.gridDim = dim3(ntiles, 1, 1);
+    if (!G) return cudaGraphExecKernelNodeSetParams(exec, node, &p);
+    // grouped sweep: (const BatchGroups G, float* pool, const BatchArgs* args, int parity)
+    void* kp[4] = {const_cast<BatchGroups*>(G), p.kernelParams[1], p.kernelParams[2], p.kernelParams[3]};
+    p.kernelParams = kp;
+    return cudaGraphExecKernelNodeSetParams(exec, node, &p);
 }
 
 cudaError_t launch_batch_sweep_tb(int T, unsigned ntiles, const int4* tiles, const BatchArgs* args, cudaStream_t s) {

@@ -112,3 +112,35 @@ def test_batch_stagnation_flag():
     ud = [torch.from_numpy(u0).cuda() for _ in range(2)]
     stats, ms, rc = batch.solve([torch.from_numpy(f).cuda()] * 2, ud, 1e-30, 10000, raise_on_fail=False)
     assert rc == -3 and all(s["stagnated"] == 1 and s["cycles"] < 200 and s["rel_res"] < 1e-11 for s in stats)
+
+
+def test_many_grid_sizes_use_the_tile_list_sweep_bit_for_bit():
+    """More distinct grid sizes than the grouped sweep takes (16): the batch runs
+    the tile-list sweep, and every problem still equals its single-plan solve
+    bit for bit."""
+    from oracle import schedule as S
+    T = 6
+    dims_list = [(30 + 3 * i, 20 + 2 * i) for i in range(18)]
+    probs, fs, u0s, plans = [], [], [], []
+    for i, dims in enumerate(dims_list):
+        km = oracle.kappa_min_dirichlet(dims)
+        omega, beta, _ = S.solve_optimal(4, km)
+        q = S.q_floor(beta)
+        order = S.order_drift(omega, q, km)
+        h = 1.0 / (max(dims) + 1)
+        probs.append(dict(dims=dims, h=h, omega=omega, q=q, order=order))
+        fs.append(W.random_field(dims, 80 + i))
+        u = W.random_field(dims, 90 + i); u[1:-1, 1:-1] = 0
+        u0s.append(u)
+        plan = srj.Plan(dims, h, omega, q, order, "mixed")
+        plan.set_temporal_depth(T)
+        plans.append(plan)
+    batch = srj.Batch(probs, temporal_depth=T)
+    ud = [torch.from_numpy(u).cuda() for u in u0s]
+    stats, ms, rc = batch.solve([torch.from_numpy(f).cuda() for f in fs], ud, 1e-10, 2000)
+    assert rc == 0
+    for plan, f, u0, u, st in zip(plans, fs, u0s, ud, stats):
+        ref = torch.from_numpy(u0).cuda()
+        st1 = plan.solve(torch.from_numpy(f).cuda(), ref, 1e-10, 2000)
+        assert st["cycles"] == st1["cycles"]
+        assert torch.equal(u, ref)
