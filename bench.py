@@ -438,19 +438,24 @@ def run_srj(args):
     fd = torch.empty_like(f)  # the caller's device buffers, allocated once (outside the timed region)
     ud = torch.empty_like(u)
     e2e_ms = []
+    e2e_split = [0.0, 0.0, 0.0]  # H2D, solve, D2H (ms, summed over steps)
     e2e_sweeps = 0
     for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a, c1, c2, b = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         a.record(stream)
         fd.copy_(f_pin, non_blocking=True)
         ud.copy_(u_pin, non_blocking=True)
+        c1.record(stream)
         st = plan.solve(fd, ud, TOL, MAX_CYCLES)
+        c2.record(stream)
         out_pin.copy_(ud, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
+        for k, (x, y) in enumerate(((a, c1), (c1, c2), (c2, b))):
+            e2e_split[k] += x.elapsed_time(y)
         e2e_sweeps += st["sweeps"]
     e2e_value = world * e2e_sweeps * pts / (sum(e2e_ms) / 1e3) / 1e9
 
@@ -495,7 +500,9 @@ def run_srj(args):
             "fp64_comparator": fp64, "speedup_vs_fp64_time_to_tol": fp64["time_to_tol_s"] / (ms_per_step / 1e3),
             "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Gupdates/s", "h2d_bytes_per_step": 2 * f_h.nbytes,
-                    "d2h_bytes_per_step": u0_h.nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+                    "d2h_bytes_per_step": u0_h.nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms),
+                    "h2d_ms": e2e_split[0] / len(e2e_ms), "solve_ms": e2e_split[1] / len(e2e_ms),
+                    "d2h_ms": e2e_split[2] / len(e2e_ms)},
             "gpu_launches": launches_per_step * args.steps, "secondary_workloads": secondary}
     if rank == 0:
         print(json.dumps(line), flush=True)
