@@ -144,3 +144,23 @@ def test_many_grid_sizes_use_the_tile_list_sweep_bit_for_bit():
         st1 = plan.solve(torch.from_numpy(f).cuda(), ref, 1e-10, 2000)
         assert st["cycles"] == st1["cycles"]
         assert torch.equal(u, ref)
+
+
+def test_repeated_solve_reuses_the_graph_bit_for_bit():
+    """A second solve with the same tolerance reuses the captured graph, whose
+    launches the first solve narrowed to its last unfinished problems: it must
+    launch every problem again and give the same bits and cycle counts."""
+    specs = [(64, 5, 21), (256, 10, 23), (128, 6, 25), (64, 9, 27)]
+    probs, fs, u0s = zip(*[_problem(*s) for s in specs])
+    batch = srj.Batch(list(probs), temporal_depth=8)
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    runs = []
+    for _ in range(2):
+        ud = [torch.from_numpy(u).cuda() for u in u0s]
+        stats, ms, rc = batch.solve(fd, ud, 1e-10, 200)
+        assert rc == 0
+        runs.append((ud, [(s["cycles"], s["sweeps"]) for s in stats]))
+    # the problems finish after different numbers of phases, so the first solve narrows its launches
+    assert runs[0][1] == runs[1][1] and len({sw for _, sw in runs[0][1]}) > 1
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert torch.equal(a, b)
