@@ -249,11 +249,15 @@ int srj_schedule_order(int P, const double *omega, const int32_t *q, double kapp
  * SRJ schedule, solved together in mixed precision (FP32 M-cycles on the defect
  * equation inside FP64 correction, as SRJ_PREC_MIXED).  One phase advances every
  * unfinished problem by up to T steps of its own cycle order in one blocked
- * sweep launch over the tiles of all problems, then updates, checks the
- * residual of and restarts the problems whose cycle ended.  A CUDA graph of
+ * sweep launch over the tiles of the unfinished problems, then updates, checks
+ * the residual of and restarts the problems whose cycle ended.  A CUDA graph of
  * several phases is replayed until every problem has converged, failed, or run
- * max_cycles cycles.  The paper's method per problem is Sect. 2 / 3.1 / 5.1; the
- * batching is this library's.
+ * max_cycles cycles; between replays its launches are narrowed to the problems
+ * still iterating.  Batches with at most 16 distinct grid sizes and at most 1024
+ * problems use a faster sweep whose blocks locate their tiles from the launch
+ * parameters; the results are the same bit for bit either way, and equal those
+ * of single mixed-precision plans with the same temporal depth.  The paper's
+ * method per problem is Sect. 2 / 3.1 / 5.1; the batching is this library's.
  */
 typedef struct srj_batch *srj_batch_t;
 
