@@ -3,7 +3,9 @@
 Tolerances:
 * FP64 sweeps and the FP64 residual use the oracle's operation order without
   FMA contraction, so iterates and residual vectors must be bit-identical.
-  Norms are parallel reductions: relative 1e-12.
+  Norms are parallel reductions: relative 1e-12 (at the full sizes, against a
+  pairwise sum of the identical residual field; the oracle's one-by-one sum of
+  N squares is then held to the recursive-summation bound (N - 1) 2^-53).
 * FP32 sweep: per point, |gpu - oracle| <= 8 eps32 * (|u| + c (sum|nbrs| + |h^2 f| + 2d |u|))
   (a handful of FP32 roundings of the terms of one step).
 * Mixed-precision solves: final relative residual, recomputed by the oracle
@@ -65,6 +67,44 @@ def test_fp64_sweeps_bit_identical(dims):
         ref = u.copy()
         oracle.steps(dims, h, seq, f, ref, first=first, count=count)
         assert np.array_equal(ud.cpu().numpy(), ref), (dims, first, count)
+
+
+@pytest.mark.parametrize("case", ["2d_4096_P10", "3d_512_P12"])
+def test_full_size_fp64_steps_and_residual_bit_identical(case):
+    """The FP64 path at the workloads' full sizes, in the launch configuration of
+    the FP64 comparator (table schedule, plan order): a few steps from the
+    start of the cycle and around its largest weight give the oracle's iterate
+    bit for bit, and so does the residual field of the result."""
+    if case == "2d_4096_P10":
+        n, P = 4096, 10
+        dims = (n, n)
+        f, u = W.random_smooth_problem_2d(n, 2)
+    else:
+        n, P = 512, 12
+        dims = (n, n, n)
+        f, u = W.gaussian_blobs_3d(n, 3)
+    plan = srj.Plan.from_table(dims, P, "fp64")
+    row = srj.schedules.lookup(len(dims), n, P)
+    seq = oracle.omega_sequence(row["omega"], row["order"])
+    k = int(np.argmax(seq))
+    fd = dev(f)
+    ref = u.copy()
+    ud = dev(u)
+    for first, count in [(0, 2), (max(k - 1, 0), 3)]:
+        plan.steps(fd, ud, first, count)
+        oracle.steps(dims, plan.h, seq, f, ref, first=first, count=count)
+        assert np.array_equal(ud.cpu().numpy(), ref), (case, first, count)
+    rd = torch.empty_like(ud)
+    l2, linf = plan.residual(fd, ud, rd)
+    l2o, linfo, r = oracle.residual(dims, plan.h, f, ref, want_r=True)
+    assert np.array_equal(rd.cpu().numpy(), r)
+    assert linf == linfo
+    # The norms sum ~N squares in different orders.  Against a pairwise sum of the
+    # (identical) residual field: the library's blocked reduction within 1e-12, the
+    # oracle's one-by-one sum within the recursive-summation bound (N - 1) * 2^-53.
+    acc = math.sqrt(float(np.sum(np.square(r))))
+    assert math.isclose(l2, acc, rel_tol=1e-12), (l2, acc)
+    assert math.isclose(l2o, acc, rel_tol=r.size * 2.0 ** -53), (l2o, acc)
 
 
 @pytest.mark.parametrize("dims", [(37, 23), (1, 1), (64, 64), (13, 11, 9), (2, 3, 1)])
