@@ -13,6 +13,9 @@
 //   3. FP64 update u += e / s for the problems whose cycle ended;
 //   4. FP64 residual r = b - A u for them (written as FP32 r * s, with L2 / max
 //      partial sums per row block).
+// Launches 3 and 4 walk the row blocks that launch 1 listed as due in this
+// phase, from a fixed grid of a few blocks per SM, so that a phase in which no
+// cycle ends costs them next to nothing.
 // Kernel boundaries order the phases (no device-side waits); every launch reads
 // the per-problem state from device memory, so one CUDA graph of G phases (and
 // a closing cycle-end test) is captured and replayed until no problem is
@@ -116,23 +119,34 @@ __device__ __forceinline__ void finish_cycle(const srj::BatchProb& P, srj::Batch
     }
 }
 
+// due / ndue: per phase parity, the row blocks of the problems whose cycle ends
+// with this phase's sweep (in no particular order; each row block's results go
+// to its own slots) and their number.  The update and the residual of the phase
+// walk that list; the step of the next phase, of the other parity, clears this
+// phase's count only after both have run.
 __global__ void k_batch_step(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st,
                              const double* __restrict__ partials, const float* __restrict__ cw,
-                             srj::BatchArgs* __restrict__ args, int nprob, int T, double tol, int max_cycles) {
+                             srj::BatchArgs* __restrict__ args, int nprob, int T, double tol, int max_cycles,
+                             int* __restrict__ due, int* __restrict__ ndue, int nrowblocks, int parity) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) ndue[parity ^ 1] = 0;  // the next phase's list starts empty
     if (p >= nprob) return;
     srj::BatchState s = st[p];
     const srj::BatchProb P = probs[p];
     if (s.active && s.cycle_end) finish_cycle(P, s, partials, tol, max_cycles);
     prepare_and_advance(P, s, cw, args, T);
     st[p] = s;
+    if (s.active && s.cycle_end) {
+        const int nrb = P.rb_end - P.rb_begin;
+        int* d = due + (size_t)parity * nrowblocks + atomicAdd(&ndue[parity], nrb);
+        for (int r = 0; r < nrb; ++r) d[r] = P.rb_begin + r;
+    }
 }
 
-// u += inv_scale * e on the rows of one row block, for problems at a cycle end.
-// Block b takes row block ids[b] (b itself when ids is NULL).
-__global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
-                               const int2* __restrict__ rowblocks, const int* __restrict__ ids) {
-    const int id = ids ? ids[blockIdx.x] : (int)blockIdx.x;
+// u += inv_scale * e on the rows of row block id, when its problem is at a cycle end.
+__device__ __forceinline__ void update_rowblock(const srj::BatchProb* __restrict__ probs,
+                                                const srj::BatchState* __restrict__ st,
+                                                const int2* __restrict__ rowblocks, int id) {
     const int2 rb = rowblocks[id];
     const srj::BatchState s = st[rb.x];
     if (!s.active || !s.cycle_end) return;
@@ -145,40 +159,47 @@ __global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const s
             P.u[(int64_t)y * sx + x] += s.inv_scale * (double)e[(int64_t)y * P.p32 + x + 3];
 }
 
-// r = (h^2 f + sum nbrs u) - 4 u in the oracle's operation order; optional FP32
-// defect r * scale; per-block L2 / max partials.  `all`: every active problem
-// (initial residual), otherwise only problems at a cycle end.  Block b takes
-// row block ids[b] (b itself when ids is NULL); its partials go to that row
-// block's slot.
-__global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
-                                 const int2* __restrict__ rowblocks, const int* __restrict__ ids,
-                                 double* __restrict__ partials, int write_r32, int all) {
-    __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
-    const int id = ids ? ids[blockIdx.x] : (int)blockIdx.x;
+// Row blocks due[parity][0 .. ndue[parity]) (grid-stride), or row block
+// blockIdx.x when ndue is NULL.
+__global__ void k_batch_update(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
+                               const int2* __restrict__ rowblocks, const int* __restrict__ due,
+                               const int* __restrict__ ndue, int nrowblocks, int parity) {
+    if (!ndue) { update_rowblock(probs, st, rowblocks, (int)blockIdx.x); return; }
+    const int n = ndue[parity];
+    const int* d = due + (size_t)parity * nrowblocks;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) update_rowblock(probs, st, rowblocks, d[j]);
+}
+
+// r = (h^2 f + sum nbrs u) - 4 u in the oracle's operation order on row block
+// id; optional FP32 defect r * scale; the block's L2 / max partials in the row
+// block's slot.  `all`: every active problem (initial residual), otherwise only
+// problems at a cycle end.  Uniform over the block.
+__device__ __forceinline__ void residual_rowblock(const srj::BatchProb* __restrict__ probs,
+                                                  const srj::BatchState* __restrict__ st,
+                                                  const int2* __restrict__ rowblocks, int id,
+                                                  double* __restrict__ partials, int write_r32, int all,
+                                                  double* sh_ss, double* sh_mx) {
     const int2 rb = rowblocks[id];
     const srj::BatchState s = st[rb.x];
-    const bool work = s.active && (all || s.cycle_end);
+    if (!(s.active && (all || s.cycle_end))) return;
     double ss = 0.0, mx = 0.0;
-    if (work) {
-        const srj::BatchProb P = probs[rb.x];
-        const int y1 = min(rb.y + kRowsPerBlock - 1, P.ny);
-        const int64_t sx = P.nx + 2;
-        for (int y = rb.y; y <= y1; ++y) {
-            for (int x = threadIdx.x + 1; x <= P.nx; x += blockDim.x) {
-                const int64_t q = (int64_t)y * sx + x;
-                const double uc = P.u[q];
-                double sm = __dadd_rn(P.u[q - 1], P.u[q + 1]);
-                sm = __dadd_rn(sm, P.u[q - sx]);
-                sm = __dadd_rn(sm, P.u[q + sx]);
-                const double t = __dadd_rn(sm, __dmul_rn(P.h2, P.f[q]));
-                const double r = __dsub_rn(t, __dmul_rn(4.0, uc));
-                if (write_r32) P.r32[(int64_t)y * P.p32 + x + 3] = (float)(r * s.scale);
-                ss = fma(r, r, ss);
-                mx = fmax(mx, fabs(r));
-            }
+    const srj::BatchProb P = probs[rb.x];
+    const int y1 = min(rb.y + kRowsPerBlock - 1, P.ny);
+    const int64_t sx = P.nx + 2;
+    for (int y = rb.y; y <= y1; ++y) {
+        for (int x = threadIdx.x + 1; x <= P.nx; x += blockDim.x) {
+            const int64_t q = (int64_t)y * sx + x;
+            const double uc = P.u[q];
+            double sm = __dadd_rn(P.u[q - 1], P.u[q + 1]);
+            sm = __dadd_rn(sm, P.u[q - sx]);
+            sm = __dadd_rn(sm, P.u[q + sx]);
+            const double t = __dadd_rn(sm, __dmul_rn(P.h2, P.f[q]));
+            const double r = __dsub_rn(t, __dmul_rn(4.0, uc));
+            if (write_r32) P.r32[(int64_t)y * P.p32 + x + 3] = (float)(r * s.scale);
+            ss = fma(r, r, ss);
+            mx = fmax(mx, fabs(r));
         }
     }
-    if (!work) return;  // uniform over the block
     for (int o = 16; o > 0; o >>= 1) {
         ss += __shfl_down_sync(0xffffffffu, ss, o);
         mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
@@ -192,6 +213,24 @@ __global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const
         partials[2 * id] = a;
         partials[2 * id + 1] = (a == a) ? m : a;
     }
+    __syncthreads();  // sh_ss / sh_mx are reused by the block's next row block
+}
+
+// Row blocks due[parity][0 .. ndue[parity]) (grid-stride), or row block
+// blockIdx.x when ndue is NULL.
+__global__ void k_batch_residual(const srj::BatchProb* __restrict__ probs, const srj::BatchState* __restrict__ st,
+                                 const int2* __restrict__ rowblocks, const int* __restrict__ due,
+                                 const int* __restrict__ ndue, int nrowblocks, int parity,
+                                 double* __restrict__ partials, int write_r32, int all) {
+    __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
+    if (!ndue) {
+        residual_rowblock(probs, st, rowblocks, (int)blockIdx.x, partials, write_r32, all, sh_ss, sh_mx);
+        return;
+    }
+    const int n = ndue[parity];
+    const int* d = due + (size_t)parity * nrowblocks;
+    for (int j = blockIdx.x; j < n; j += gridDim.x)
+        residual_rowblock(probs, st, rowblocks, d[j], partials, write_r32, all, sh_ss, sh_mx);
 }
 
 __global__ void k_batch_finalize(const srj::BatchProb* __restrict__ probs, srj::BatchState* __restrict__ st,
@@ -261,8 +300,10 @@ struct srj_batch {
     std::vector<int> tile_begin;  // first tile of each problem in `tiles`
     std::vector<unsigned char> launched;  // problems the graph's launches cover
     cudaGraph_t graph = nullptr;          // kept: its nodes are re-targeted between launches
-    std::vector<cudaGraphNode_t> sweep_nodes, rowblock_nodes;
-    int* d_rb_ids = nullptr;              // row blocks of the launched problems
+    std::vector<cudaGraphNode_t> sweep_nodes;
+    int* d_due = nullptr;                 // 2 x nrowblocks: row blocks due per phase parity
+    int* d_ndue = nullptr;                // 2 counts
+    int rowblock_grid = 1;                // blocks of the graph's update / residual launches
     unsigned char* d_flags = nullptr;
     unsigned char* h_flags = nullptr;
     srj::BatchProb* d_probs = nullptr;
@@ -284,7 +325,7 @@ struct srj_batch {
     ~srj_batch() {
         if (phases) cudaGraphExecDestroy(phases);
         if (graph) cudaGraphDestroy(graph);
-        cudaFree(d_rb_ids); cudaFree(d_flags);
+        cudaFree(d_due); cudaFree(d_ndue); cudaFree(d_flags);
         if (h_flags) cudaFreeHost(h_flags);
         if (cap) cudaStreamDestroy(cap);
         if (ev0) cudaEventDestroy(ev0);
@@ -312,7 +353,7 @@ cudaError_t last_node(cudaStream_t s, cudaGraphNode_t* out) {
 cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles, int parity) {
     const int pb = (b->nprob + kThreads - 1) / kThreads;
     k_batch_step<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->d_cw, b->d_args, b->nprob, b->T,
-                                         tol, max_cycles);
+                                         tol, max_cycles, b->d_due, b->d_ndue, b->nrowblocks, parity);
     cudaError_t e = b->grouped
                         ? srj::launch_batch_sweep_grouped(b->T, (unsigned)b->ntiles, b->groups, b->d_pool, b->d_args,
                                                           parity, s)
@@ -321,25 +362,19 @@ cudaError_t issue_phase(srj_batch* b, cudaStream_t s, double tol, int max_cycles
     if (e == cudaSuccess) e = last_node(s, &n);
     if (e != cudaSuccess) return e;
     b->sweep_nodes.push_back(n);
-    k_batch_update<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_rb_ids);
-    e = last_node(s, &n);
-    if (e != cudaSuccess) return e;
-    b->rowblock_nodes.push_back(n);
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_rb_ids,
-                                                        b->d_partials, 1, 0);
-    e = last_node(s, &n);
-    if (e != cudaSuccess) return e;
-    b->rowblock_nodes.push_back(n);
+    k_batch_update<<<b->rowblock_grid, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_due, b->d_ndue,
+                                                         b->nrowblocks, parity);
+    k_batch_residual<<<b->rowblock_grid, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, b->d_due,
+                                                           b->d_ndue, b->nrowblocks, parity, b->d_partials, 1, 0);
     return cudaGetLastError();
 }
 
-// Point the graph's sweep, update and residual launches at the problems flagged
-// in `want` (those still iterating at the start of the next graph launch).
-// Problems that finish during a launch keep their blocks until the next one;
-// those blocks see no steps and no cycle end and leave early.
+// Point the graph's sweep launches at the problems flagged in `want` (those
+// still iterating at the start of the next graph launch).  Problems that finish
+// during a launch keep their blocks until the next one; those blocks see no
+// steps and leave early.  (Update and residual walk the phase's due list.)
 int retarget(srj_batch* b, const unsigned char* want, cudaStream_t s) {
     if (b->launched.size() == (size_t)b->nprob && std::equal(b->launched.begin(), b->launched.end(), want)) return SRJ_OK;
-    std::vector<int> ids;
     unsigned ntiles = 0;
     srj::BatchGroups G = b->groups;
     std::vector<int4> tl;
@@ -361,21 +396,11 @@ int retarget(srj_batch* b, const unsigned char* want, cudaStream_t s) {
             if (want[p]) tl.insert(tl.end(), b->tiles.begin() + b->tile_begin[p], b->tiles.begin() + b->tile_begin[p + 1]);
         ntiles = (unsigned)tl.size();
     }
-    for (int p = 0; p < b->nprob; ++p)
-        if (want[p])
-            for (int r = b->probs[p].rb_begin; r < b->probs[p].rb_end; ++r) ids.push_back(r);
-    if (ntiles == 0 || ids.empty()) return SRJ_OK;  // nothing left to launch: the solve loop ends
-    SRJ_BCUDA(cudaMemcpyAsync(b->d_rb_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
+    if (ntiles == 0) return SRJ_OK;  // nothing left to launch: the solve loop ends
     if (!b->grouped)
         SRJ_BCUDA(cudaMemcpyAsync(b->d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, s));
     for (cudaGraphNode_t n : b->sweep_nodes)
         SRJ_BCUDA(srj::batch_sweep_set_node(b->phases, n, ntiles, b->grouped ? &G : nullptr));
-    for (cudaGraphNode_t n : b->rowblock_nodes) {
-        cudaKernelNodeParams kp{};
-        SRJ_BCUDA(cudaGraphKernelNodeGetParams(n, &kp));
-        kp.gridDim = dim3((unsigned)ids.size(), 1, 1);
-        SRJ_BCUDA(cudaGraphExecKernelNodeSetParams(b->phases, n, &kp));
-    }
     b->launched.assign(want, want + b->nprob);
     return SRJ_OK;
 }
@@ -384,12 +409,8 @@ int capture_phases(srj_batch* b, double tol, int max_cycles, cudaStream_t s) {
     if (b->phases) { cudaGraphExecDestroy(b->phases); b->phases = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->sweep_nodes.clear();
-    b->rowblock_nodes.clear();
     b->launched.clear();
-    // the captured launches cover every problem: identity row-block list and full tile list
-    std::vector<int> ids(b->nrowblocks);
-    for (int i = 0; i < b->nrowblocks; ++i) ids[i] = i;
-    SRJ_BCUDA(cudaMemcpyAsync(b->d_rb_ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
+    // the captured sweeps cover every problem: full tile list
     SRJ_BCUDA(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(int4) * b->tiles.size(), cudaMemcpyHostToDevice, s));
     cudaGraph_t graph = nullptr;
     SRJ_BCUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -403,10 +424,10 @@ int capture_phases(srj_batch* b, double tol, int max_cycles, cudaStream_t s) {
         err = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); b->sweep_nodes.clear(); b->rowblock_nodes.clear(); SRJ_BCUDA(err); }
+    if (err != cudaSuccess) { if (graph) cudaGraphDestroy(graph); b->sweep_nodes.clear(); SRJ_BCUDA(err); }
     SRJ_BCUDA(e2);
     cudaError_t e3 = cudaGraphInstantiate(&b->phases, graph, 0);
-    if (e3 != cudaSuccess) { cudaGraphDestroy(graph); b->sweep_nodes.clear(); b->rowblock_nodes.clear(); SRJ_BCUDA(e3); }
+    if (e3 != cudaSuccess) { cudaGraphDestroy(graph); b->sweep_nodes.clear(); SRJ_BCUDA(e3); }
     b->graph = graph;
     b->launched.assign(b->nprob, 1);
     b->graph_tol = tol;
@@ -579,6 +600,11 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
         if (tb != b->ntiles) return bail(bfail(SRJ_ERR_INVALID_ARG, "internal: grouped tile count %lld != %d", (long long)tb, b->ntiles));
     }
     if (cudaGetDevice(&b->device) != cudaSuccess) return bail(bfail(SRJ_ERR_CUDA, "no CUDA device"));
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || sms < 1) sms = 1;
+        b->rowblock_grid = std::max(1, std::min(b->nrowblocks, 4 * sms));
+    }
     auto alloc = [](void** ptr, size_t by) { return cudaMalloc(ptr, by) == cudaSuccess; };
     bool ok = alloc((void**)&b->d_pool, sizeof(float) * pool_floats) &&
               alloc((void**)&b->d_probs, sizeof(srj::BatchProb) * nprob) &&
@@ -589,7 +615,8 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
               alloc((void**)&b->d_cw, sizeof(float) * cw.size()) &&
               alloc((void**)&b->d_partials, sizeof(double) * 2 * rowblocks.size()) &&
               alloc((void**)&b->d_count, sizeof(int)) &&
-              alloc((void**)&b->d_rb_ids, sizeof(int) * rowblocks.size()) &&
+              alloc((void**)&b->d_due, sizeof(int) * 2 * rowblocks.size()) &&
+              alloc((void**)&b->d_ndue, sizeof(int) * 2) &&
               alloc((void**)&b->d_flags, (size_t)nprob);
     if (!ok) { cudaGetLastError(); return bail(bfail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
     for (int p = 0; p < nprob; ++p) {
@@ -660,11 +687,11 @@ int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, dou
     const int pb = (b->nprob + kThreads - 1) / kThreads;
     const int mc = (int)std::max<int64_t>(max_cycles, 1);
     // initial residual (norms, then the scaled FP32 defect)
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, b->d_partials,
-                                                        0, 1);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, nullptr,
+                                                        b->nrowblocks, 0, b->d_partials, 0, 1);
     k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit0, tol, mc);
-    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, b->d_partials,
-                                                        1, 1);
+    k_batch_residual<<<b->nrowblocks, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_rowblocks, nullptr, nullptr,
+                                                        b->nrowblocks, 0, b->d_partials, 1, 1);
     k_batch_finalize<<<pb, kThreads, 0, s>>>(b->d_probs, b->d_state, b->d_partials, b->nprob, kFinInit1, tol, mc);
     SRJ_BCUDA(cudaGetLastError());
     if (b->graph_tol != tol || b->graph_max_cycles != mc || !b->phases) {
@@ -680,6 +707,7 @@ int srj_batch_solve(srj_batch_t b, const double* const* f, double* const* u, dou
     int64_t max_phases = 0;
     for (int m : b->M) max_phases = std::max<int64_t>(max_phases, (int64_t)m);
     max_phases = max_phases * mc + kPhasesPerGraph;
+    SRJ_BCUDA(cudaMemsetAsync(b->d_ndue, 0, 2 * sizeof(int), s));  // both due lists start empty
     SRJ_BCUDA(cudaEventRecord(b->ev0, s));
     int64_t phases = 0;
     if (max_cycles > 0) {
