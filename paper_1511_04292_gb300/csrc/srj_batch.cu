@@ -298,7 +298,7 @@ struct srj_batch {
     std::vector<int> gid, gz;   // group and group-local index of each problem
     std::vector<int4> tiles;    // tile list (problem, tile x, tile y) of every problem
     std::vector<int> tile_begin;  // first tile of each problem in `tiles`
-    std::vector<unsigned char> launched;  // problems the graph's launches cover
+    std::vector<unsigned char> launched;  // problems the graph's sweep launches cover
     cudaGraph_t graph = nullptr;          // kept: its nodes are re-targeted between launches
     std::vector<cudaGraphNode_t> sweep_nodes;
     int* d_due = nullptr;                 // 2 x nrowblocks: row blocks due per phase parity
