@@ -164,6 +164,68 @@ def test_fp32_order_is_a_valid_cycle_with_no_more_modelled_noise():
     assert S.fp32_cycle_noise(omega, bad, km) > 1.0
 
 
+def _cycle_float(seq, r, dtype):
+    """One SRJ cycle on the 2-D defect equation A e = r from e = 0 (e = 0 on the
+    boundary), every operation rounded to `dtype` (numpy does not contract)."""
+    e = np.zeros_like(r, dtype=dtype)
+    rr = r.astype(dtype)
+    four = dtype(4.0)
+    for w in seq:
+        nb = ((e[1:-1, :-2] + e[1:-1, 2:]) + e[:-2, 1:-1]) + e[2:, 1:-1]
+        t = (nb + rr[1:-1, 1:-1]) - four * e[1:-1, 1:-1]
+        e2 = e.copy()
+        e2[1:-1, 1:-1] = e[1:-1, 1:-1] + dtype(w / 4.0) * t
+        e = e2
+    return e
+
+
+def test_fp32_noise_model_against_brute_force_fp32_cycles():
+    """The FP32 noise model that picks the cycle order, against brute force: one
+    cycle in float32 and in float64 on a 128^2 grid from a white residual; the
+    residual of the difference, ||A (e32 - e64)|| / ||r||, for the drift order
+    with m = 0..36 copies of omega_P moved to the tail and for the reversed
+    order.  The measured noise spans 20 decades; the model must rank the orders
+    as measured (Spearman >= 0.95), stay within a factor 10 of every measurement,
+    and the order order_fp32 picks must be within 1.5x of the quietest one."""
+    import paper_1511_04292_gb300.schedules as sch
+    from scipy.stats import spearmanr
+    n, P = 128, 7
+    row = sch.lookup(2, n, P)
+    omega, q = np.asarray(row["omega"]), np.asarray(row["q"])
+    km = oracle.kappa_min_dirichlet((n, n))
+    base = [int(v) for v in S.order_drift(omega, q, km)]
+    small = P - 1
+    body = base[:-min(S.TAIL_STEPS, int(q[-1]))]
+    tail0 = len(base) - len(body)
+    pos = [i for i, v in enumerate(body) if v == small]
+    cands = {"reversed": base[::-1]}
+    for m in range(0, 40, 4):
+        drop = set(pos[:m])
+        cands[m] = [v for i, v in enumerate(body) if i not in drop] + [small] * (tail0 + m)
+    rng = np.random.default_rng(5)
+    r = np.zeros((n + 2, n + 2))
+    r[1:-1, 1:-1] = rng.standard_normal((n, n))
+    r = r.astype(np.float32).astype(np.float64)
+
+    def A(e):
+        return 4 * e[1:-1, 1:-1] - (((e[1:-1, :-2] + e[1:-1, 2:]) + e[:-2, 1:-1]) + e[2:, 1:-1])
+
+    model, meas = [], []
+    for o in cands.values():
+        seq = omega[np.asarray(o)]
+        d = _cycle_float(seq, r, np.float32).astype(np.float64) - _cycle_float(seq, r, np.float64)
+        meas.append(np.linalg.norm(A(d)) / np.linalg.norm(r[1:-1, 1:-1]))
+        model.append(S.fp32_cycle_noise(omega, o, km))
+    model, meas = np.array(model), np.array(meas)
+    assert np.all(np.isfinite(meas)) and meas.max() / meas.min() > 1e15
+    assert spearmanr(model, meas).correlation >= 0.95
+    assert np.all((meas / model > 0.1) & (meas / model < 10.0)), meas / model
+    pick = [int(v) for v in S.order_fp32(omega, q, km)]
+    seq = omega[np.asarray(pick)]
+    d = _cycle_float(seq, r, np.float32).astype(np.float64) - _cycle_float(seq, r, np.float64)
+    assert np.linalg.norm(A(d)) / np.linalg.norm(r[1:-1, 1:-1]) <= 1.5 * meas.min()
+
+
 def test_integer_scheme_contracts():
     """Sect. 4.3: after the floor conversion the cycle factor stays below 1 on
     [kappa_m, 2]; a scheme that over-weights the largest omega does not."""
