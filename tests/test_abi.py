@@ -115,3 +115,25 @@ def test_packaged_schedules_contract_and_match_their_order():
         assert row["log10_cycle_factor_max"] < 0
         assert np.bincount(row["order"], minlength=P).tolist() == row["q"].tolist()
         assert abs(row["kappa_min"] - oracle.kappa_min_dirichlet([n] * nd)) < 1e-15
+
+
+@pytest.mark.parametrize("bad", ["empty", "dims", "h", "P", "omega", "q", "order", "depth", "contraction"])
+def test_batch_argument_checks_before_touching_the_gpu(bad):
+    """srj_batch_create validates every problem before its first CUDA call:
+    bad arguments give SRJ_ERR_INVALID_ARG, a scheme that does not contract on
+    its grid SRJ_ERR_BAD_SCHEDULE (no GPU is needed to see either)."""
+    ok = dict(dims=(40, 30), h=1 / 41, omega=[2.0, 0.7], q=[1, 3], order=[1, 0, 1, 1])
+    probs = [dict(ok), dict(ok, dims=(17, 9))]
+    depth = 0
+    if bad == "empty": probs = []
+    if bad == "dims": probs[1]["dims"] = (0, 9)
+    if bad == "h": probs[1]["h"] = float("nan")
+    if bad == "P": probs[1]["omega"], probs[1]["q"], probs[1]["order"] = [], [], None
+    if bad == "omega": probs[1]["omega"] = [2.0, -0.7]
+    if bad == "q": probs[1]["q"] = [1, 0]
+    if bad == "order": probs[1]["order"] = [1, 1, 1, 1]
+    if bad == "depth": depth = 9
+    if bad == "contraction": probs[1]["omega"], probs[1]["q"], probs[1]["order"] = [100.0, 0.6], [50, 1], None
+    with pytest.raises(srj.SRJError) as ei:
+        srj.Batch(probs, temporal_depth=depth)
+    assert ei.value.status == (-2 if bad == "contraction" else -1), (bad, str(ei.value))
