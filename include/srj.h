@@ -200,6 +200,18 @@ int srj_solve(srj_plan_t plan, const double *f, double *u, double tol, int64_t m
               void *stream, srj_stats_t *stats);
 
 /*
+ * srj_solve_host -- srj_solve on HOST arrays: f and u (same padded float64
+ * layout; pinned memory for full copy bandwidth) are copied to device staging
+ * buffers that the plan allocates on the first call and keeps, the solve runs
+ * there, and u is copied back (also after SRJ_ERR_NOT_CONVERGED or
+ * SRJ_ERR_DIVERGED, as srj_solve leaves its iterate).  Copies and solve are on
+ * `stream`; blocks the host until u is back.  SRJ_ERR_NO_MEMORY if the staging
+ * buffers cannot be allocated.
+ */
+int srj_solve_host(srj_plan_t plan, const double *f, double *u, double tol, int64_t max_cycles,
+                   void *stream, srj_stats_t *stats);
+
+/*
  * srj_steps -- apply `count` consecutive steps of the cycle order, starting at
  * position `first` (mod M), to u in place, without residual checks.  FP64 plans
  * use the FP64 sweep; mixed plans round u and h^2 f to float32, apply the FP32

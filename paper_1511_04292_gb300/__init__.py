@@ -41,6 +41,21 @@ def _dev_ptr(t, shape, name, writable=False):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(a, shape, name, writable=False):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+            raise TypeError("%s must be a C-contiguous float64 array" % name)
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError("%s must have shape %s (got %s)" % (name, tuple(shape), tuple(a.shape)))
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if not isinstance(a, torch.Tensor) or a.is_cuda or a.dtype != torch.float64:
+        raise TypeError("%s must be a float64 host array (numpy or CPU tensor)" % name)
+    if tuple(a.shape) != tuple(shape) or not a.is_contiguous():
+        raise ValueError("%s must be contiguous with shape %s (got %s)" % (name, tuple(shape), tuple(a.shape)))
+    return ctypes.c_void_p(a.data_ptr())
+
+
 def kappa_min(dims):
     """Smallest eigenvalue of D^-1 A for a Dirichlet grid (computed by the library)."""
     d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
@@ -152,6 +167,19 @@ class Plan:
         st = Stats()
         rc = self._lib.srj_solve(self._h, _dev_ptr(f, self.shape, "f"), _dev_ptr(u, self.shape, "u", True),
                                  float(tol), int(max_cycles), _stream_ptr(stream), ctypes.byref(st))
+        out = st.as_dict()
+        out["status"] = rc
+        if raise_on_fail:
+            check(rc)
+        return out
+
+    def solve_host(self, f, u, tol, max_cycles, stream=None, raise_on_fail=True):
+        """solve() on host arrays (float64, contiguous, padded shape; numpy or CPU
+        tensors, pinned for full copy bandwidth): the library copies f and u to
+        the device, solves, and copies u back in place."""
+        st = Stats()
+        rc = self._lib.srj_solve_host(self._h, _host_ptr(f, self.shape, "f"), _host_ptr(u, self.shape, "u", True),
+                                      float(tol), int(max_cycles), _stream_ptr(stream), ctypes.byref(st))
         out = st.as_dict()
         out["status"] = rc
         if raise_on_fail:

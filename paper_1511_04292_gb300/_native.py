@@ -109,6 +109,7 @@ SIGNATURES = {
     "srj_plan_sweep_variant": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "srj_plan_autotune": (_I, [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "srj_solve": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
+    "srj_solve_host": (_I, [_VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
     "srj_steps": (_I, [_VP, _VP, _VP, _I64, _I64, _VP]),
     "srj_residual": (_I, [_VP, _VP, _VP, _VP, _DP, _DP, _VP]),
     "srj_boundary_adjoint": (_I, [_VP, _VP, _VP, _VP]),

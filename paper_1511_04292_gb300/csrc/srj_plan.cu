@@ -332,6 +332,7 @@ struct srj_plan {
     int variant = 0;     // blocked sweep: 0 = one block per tile, 1 = persistent with cp.async prefetch
     int sm_count = 152;
     float* e_final = nullptr;  // buffer holding the correction after one cycle
+    double *host_f = nullptr, *host_u = nullptr;  // device staging of srj_solve_host (allocated on first use)
 
     cudaStream_t cap = nullptr;             // private stream used for graph capture
     cudaGraphExec_t cycle_exec[2] = {nullptr, nullptr};  // start buffer a / b
@@ -346,6 +347,7 @@ struct srj_plan {
         cudaFree(ea); cudaFree(eb); cudaFree(r32);
         cudaFree(ns.partials); cudaFree(ns.counter); cudaFree(ns.result);
         cudaFree(mask);
+        cudaFree(host_f); cudaFree(host_u);
         if (host_norms) cudaFreeHost(host_norms);
     }
 };
@@ -777,6 +779,31 @@ int srj_solve(srj_plan_t p, const double* f, double* u, double tol, int64_t max_
     int rc = check_plan(p);
     if (rc) return rc;
     return solve_impl(p, f, p->h2, u, tol, max_cycles, stream, stats);
+}
+
+int srj_solve_host(srj_plan_t p, const double* f, double* u, double tol, int64_t max_cycles, void* stream,
+                   srj_stats_t* stats) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!f || !u) return fail(SRJ_ERR_INVALID_ARG, "f and u must be non-NULL");
+    const size_t by64 = sizeof(double) * (size_t)p->g.n64;
+    if (!p->host_f) {
+        if (cudaMalloc(&p->host_f, by64) != cudaSuccess || cudaMalloc(&p->host_u, by64) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p->host_f);
+            cudaFree(p->host_u);
+            p->host_f = p->host_u = nullptr;
+            return fail(SRJ_ERR_NO_MEMORY, "device staging buffers for host arrays");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SRJ_CUDA(cudaMemcpyAsync(p->host_f, f, by64, cudaMemcpyHostToDevice, s));
+    SRJ_CUDA(cudaMemcpyAsync(p->host_u, u, by64, cudaMemcpyHostToDevice, s));
+    rc = solve_impl(p, p->host_f, p->h2, p->host_u, tol, max_cycles, stream, stats);
+    if (rc != SRJ_OK && rc != SRJ_ERR_NOT_CONVERGED && rc != SRJ_ERR_DIVERGED) return rc;
+    SRJ_CUDA(cudaMemcpyAsync(u, p->host_u, by64, cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return rc;
 }
 
 int srj_gradient(srj_plan_t p, const double* grad_u, double* lambda, double* grad_f, double* grad_g, double tol,

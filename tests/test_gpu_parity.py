@@ -255,6 +255,30 @@ def test_boundary_adjoint_matches_dense_transpose():
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_solve_host_equals_device_solve(prec):
+    """srj_solve_host (host arrays, copies inside the call) gives the device
+    solve's iterate bit for bit, for numpy and pinned CPU tensors, and copies
+    the iterate back also when the solve stops unconverged."""
+    n = 256
+    dims = (n, n)
+    f, u0 = W.random_smooth_problem_2d(n, 2)
+    plan = srj.Plan.from_table(dims, 8, prec)
+    for tol, cycles in [(1e-10, 200), (1e-30, 1)]:
+        ud = dev(u0)
+        st = plan.solve(dev(f), ud, tol, cycles, raise_on_fail=False)
+        ref = ud.cpu().numpy()
+        uh = u0.copy()
+        sth = plan.solve_host(f, uh, tol, cycles, raise_on_fail=False)
+        assert sth["status"] == st["status"] and sth["cycles"] == st["cycles"]
+        assert np.array_equal(uh, ref)
+        ut = torch.from_numpy(u0.copy()).pin_memory()
+        plan.solve_host(torch.from_numpy(f).pin_memory(), ut, tol, cycles, raise_on_fail=False)
+        assert np.array_equal(ut.numpy(), ref)
+    with pytest.raises(TypeError):
+        plan.solve_host(dev(f), u0.copy(), 1e-10, 10)
+
+
 def test_full_size_workload2_mixed_solve():
     """Workload 2 at full size (4096^2, P = 10, mixed, tol 1e-10) in the launch
     configuration the benchmark times: the oracle's residual of the returned u
