@@ -89,7 +89,8 @@ typedef struct srj_stats {
  * srj_plan_create -- build an SRJ plan for one grid and one schedule.
  *   ndim       2 or 3.
  *   dims       interior points per axis, dims[0] = nx (fastest), dims[1] = ny
- *              [, dims[2] = nz]; each >= 1.  Host pointer, copied.
+ *              [, dims[2] = nz]; each in 1..2^30, dims[1] <= 262140 (launch
+ *              grid limit), at most 2^36 points in all.  Host pointer, copied.
  *   h          mesh spacing (> 0, finite).
  *   P          number of levels, 1 <= P <= 32.
  *   omega      P weights omega_1..omega_P (Sect. 2; any order, each finite and

@@ -64,7 +64,7 @@ def test_plan_rejects_non_contracting_scheme_before_touching_the_gpu():
     assert b"does not contract" in srj.lib().srj_last_error()
 
 
-@pytest.mark.parametrize("bad", ["ndim", "dims", "h", "P", "omega", "q", "order", "precision"])
+@pytest.mark.parametrize("bad", ["ndim", "dims", "dims_max", "points", "h", "P", "omega", "q", "order", "precision"])
 def test_plan_argument_checks(bad):
     w = _arr([2.0, 0.7], np.float64)
     q = _arr([1, 3], np.int32)
@@ -72,6 +72,8 @@ def test_plan_argument_checks(bad):
     args = dict(ndim=2, dims=(ctypes.c_int64 * 2)(8, 8), h=0.1, P=2, omega=w, q=q, order=order, precision=0)
     if bad == "ndim": args["ndim"] = 4
     if bad == "dims": args["dims"] = (ctypes.c_int64 * 2)(0, 8)
+    if bad == "dims_max": args["dims"] = (ctypes.c_int64 * 2)(8, 262141)  # dims[1] <= 262140 (launch grid)
+    if bad == "points": args["dims"] = (ctypes.c_int64 * 2)(1 << 20, 1 << 17)  # more than 2^36 points
     if bad == "h": args["h"] = -1.0
     if bad == "P": args["P"] = 0
     if bad == "omega": args["omega"] = _arr([2.0, float("nan")], np.float64)
@@ -117,7 +119,7 @@ def test_packaged_schedules_contract_and_match_their_order():
         assert abs(row["kappa_min"] - oracle.kappa_min_dirichlet([n] * nd)) < 1e-15
 
 
-@pytest.mark.parametrize("bad", ["empty", "dims", "h", "P", "omega", "q", "order", "depth", "contraction"])
+@pytest.mark.parametrize("bad", ["empty", "dims", "dims_max", "h", "P", "omega", "q", "order", "depth", "contraction"])
 def test_batch_argument_checks_before_touching_the_gpu(bad):
     """srj_batch_create validates every problem before its first CUDA call:
     bad arguments give SRJ_ERR_INVALID_ARG, a scheme that does not contract on
@@ -127,6 +129,7 @@ def test_batch_argument_checks_before_touching_the_gpu(bad):
     depth = 0
     if bad == "empty": probs = []
     if bad == "dims": probs[1]["dims"] = (0, 9)
+    if bad == "dims_max": probs[1]["dims"] = (65537, 9)
     if bad == "h": probs[1]["h"] = float("nan")
     if bad == "P": probs[1]["omega"], probs[1]["q"], probs[1]["order"] = [], [], None
     if bad == "omega": probs[1]["omega"] = [2.0, -0.7]
