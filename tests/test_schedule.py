@@ -226,6 +226,44 @@ def test_fp32_noise_model_against_brute_force_fp32_cycles():
     assert np.linalg.norm(A(d)) / np.linalg.norm(r[1:-1, 1:-1]) <= 1.5 * meas.min()
 
 
+def test_cycle_factor_bounds_the_dense_cycle_matrix():
+    """Brute force on a 12 x 10 Dirichlet grid: the error of one SRJ cycle is
+    multiplied by E = prod_k (I - omega_k D^-1 A) (dense, in the cycle order).
+    Its spectral radius equals the largest |prod_i (1 - omega_i kappa)^q_i| over
+    the grid's eigenvalues kappa, and max_cycle_factor, which samples the whole
+    interval [kappa_min, 2], bounds it from above."""
+    nx, ny = 12, 10
+    N = nx * ny
+    A = np.zeros((N, N))
+    for y in range(ny):
+        for x in range(nx):
+            i = y * nx + x
+            A[i, i] = 4.0
+            for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                if 0 <= x + dx < nx and 0 <= y + dy < ny:
+                    A[i, (y + dy) * nx + x + dx] = -1.0
+    J = A / 4.0  # D^-1 A
+    kap = np.linalg.eigvalsh(J)
+    km = oracle.kappa_min_dirichlet((nx, ny))
+    assert abs(kap.min() - km) < 1e-12
+    omega, beta, _ = S.solve_optimal(3, km)
+    q = S.q_floor(beta)
+    order = S.order_drift(omega, q, km)
+    E = np.eye(N)
+    for k in order:
+        E = (np.eye(N) - omega[k] * J) @ E
+    rho = np.max(np.abs(np.linalg.eigvals(E)))
+    per_mode = np.max(np.abs(np.prod([(1.0 - w * kap) ** qq for w, qq in zip(omega, q)], axis=0)))
+    assert abs(np.log10(rho) - np.log10(per_mode)) < 1e-6
+    assert np.log10(rho) <= S.max_cycle_factor(omega, q, km) + 1e-9
+    assert S.max_cycle_factor(omega, q, km) < 0
+    # textbook special case with the maximum at the low end only: damped Jacobi (P = 1,
+    # omega = 0.8) has spectral radius 1 - 0.8 kappa_min (|1 - 0.8 kappa_max| is smaller)
+    rho_j = np.max(np.abs(np.linalg.eigvals(np.eye(N) - 0.8 * J)))
+    assert abs(rho_j - (1.0 - 0.8 * km)) < 1e-12
+    assert abs(S.max_cycle_factor([0.8], [1], km) - np.log10(rho_j)) < 1e-12
+
+
 def test_integer_scheme_contracts():
     """Sect. 4.3: after the floor conversion the cycle factor stays below 1 on
     [kappa_m, 2]; a scheme that over-weights the largest omega does not."""
