@@ -16,6 +16,8 @@
 // each operation rounded once, in this order (the FP64 oracle's order, so the
 // two agree bit for bit).  The SRJ cycle is that of the Poisson plans (Sect. 2).
 #include "srj_internal.h"
+
+#include <atomic>
 #include "../../include/srj.h"
 
 #include <algorithm>
@@ -453,14 +455,14 @@ cudaError_t sph_tb_attr() {
 
 cudaError_t sph_tb_prepare() {
     // kernel attributes are per device: set them once on each device used
-    static bool done[64] = {};
+    static std::atomic<bool> done[64] = {};  // idempotent setup; concurrent first calls both set
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (done[dev]) return cudaSuccess;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     cudaError_t r[7] = {sph_tb_attr<2>(), sph_tb_attr<3>(), sph_tb_attr<4>(), sph_tb_attr<5>(),
                         sph_tb_attr<6>(), sph_tb_attr<7>(), sph_tb_attr<8>()};
     for (cudaError_t x : r) if (x != cudaSuccess) return x;
-    done[dev] = true;
+    done[dev].store(true, std::memory_order_release);
     return cudaSuccess;
 }
 

@@ -17,6 +17,8 @@
 // expression, so T blocked steps reproduce T unblocked steps bit for bit.
 #include "srj_internal.h"
 
+#include <atomic>
+
 #include <algorithm>
 
 namespace srj {
@@ -624,15 +626,15 @@ void launch_batch_grp_T(unsigned ntiles, cudaStream_t s, const BatchGroups& G, f
 
 cudaError_t tb_prepare() {
     // kernel attributes are per device: set them once on each device used
-    static bool done[64] = {};
+    static std::atomic<bool> done[64] = {};  // idempotent setup; concurrent first calls both set
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (done[dev]) return cudaSuccess;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     cudaError_t r[8] = {set_attr<1>(), set_attr<2>(), set_attr<3>(), set_attr<4>(),
                         set_attr<5>(), set_attr<6>(), set_attr<7>(), set_attr<8>()};
     for (cudaError_t x : r) if (x != cudaSuccess) e = x;
-    if (e == cudaSuccess) done[dev] = true;
+    if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
     return e;
 }
 

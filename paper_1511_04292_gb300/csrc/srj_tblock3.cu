@@ -22,6 +22,8 @@
 // 64 output planes costs 2T extra plane iterations of pipeline fill.
 #include "srj_internal.h"
 
+#include <atomic>
+
 #include <algorithm>
 
 namespace srj {
@@ -231,15 +233,15 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
 
 cudaError_t tb3_prepare() {
     // kernel attributes are per device: set them once on each device used
-    static bool done[64] = {};
+    static std::atomic<bool> done[64] = {};  // idempotent setup; concurrent first calls both set
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (done[dev]) return cudaSuccess;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_sweep3_f32_tb<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<2>::kSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep3_f32_tb<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::kSmem);
-    if (e == cudaSuccess) done[dev] = true;
+    if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
     return e;
 }
 
