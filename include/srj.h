@@ -151,7 +151,7 @@ int srj_plan_temporal_depth(srj_plan_t plan, int *T);
 
 /*
  * srj_plan_autotune -- time the plan's sweep for every admissible temporal depth
- * and sweep variant on its own workspaces (a few hundred steps each, CUDA
+ * and sweep variant (a library service; the paper has no counterpart) on its own workspaces (a few hundred steps each, CUDA
  * events on `stream`), keep the fastest and report it (best_T, microseconds per step; either output
  * may be NULL).  The workspaces' contents are overwritten; srj_solve resets
  * them.  Blocks until done.
@@ -183,8 +183,12 @@ int srj_plan_set_operator(srj_plan_t plan, double sigma, const unsigned char *ma
 int srj_plan_order(srj_plan_t plan, int32_t *order_out);
 
 /*
- * srj_solve -- run SRJ cycles until ||r||_2 / ||r_0||_2 <= tol (checked at cycle
- * ends) or max_cycles cycles have run.
+ * srj_solve -- run SRJ cycles (Sect. 2: the M = sum q_i weighted-Jacobi steps of
+ * Eq. 2nd-order_CD with the Poisson source of Sect. 5.1, in the plan's order)
+ * until ||r||_2 / ||r_0||_2 <= tol (checked at cycle ends, the Sect. 4.1 monitor
+ * taken on the residual) or max_cycles cycles have run.  Mixed plans run each
+ * cycle in FP32 on the defect equation and correct u in FP64 (a library design;
+ * the cycle is the same linear map, Sect. 2).
  *   f      device, padded layout, float64 (ghost layer ignored).
  *   u      device, padded layout, float64: on entry the initial guess u0 with
  *          the Dirichlet data in its ghost layer; on return the iterate.
@@ -213,8 +217,9 @@ int srj_solve_host(srj_plan_t plan, const double *f, double *u, double tol, int6
                    void *stream, srj_stats_t *stats);
 
 /*
- * srj_steps -- apply `count` consecutive steps of the cycle order, starting at
- * position `first` (mod M), to u in place, without residual checks.  FP64 plans
+ * srj_steps -- apply `count` consecutive steps of the cycle order (Sect. 2; each
+ * step Eq. 2nd-order_CD with the Sect. 5.1 source), starting at position
+ * `first` (mod M), to u in place, without residual checks.  FP64 plans
  * use the FP64 sweep; mixed plans round u and h^2 f to float32, apply the FP32
  * sweep and write the float32 iterate back to u as float64.  Used to compare
  * iterates at equal sweep counts.
@@ -222,7 +227,9 @@ int srj_solve_host(srj_plan_t plan, const double *f, double *u, double tol, int6
 int srj_steps(srj_plan_t plan, const double *f, double *u, int64_t first, int64_t count, void *stream);
 
 /*
- * srj_residual -- r = b - A_h u on the interior (FP64), its L2 and max norms.
+ * srj_residual -- r = b - A_h u on the interior (FP64), its L2 and max norms
+ * (the discrete Poisson operator of Sect. 5.1; the convergence monitor of
+ * Sect. 4.1 taken on the residual).
  *   r_out  device padded float64 array or NULL (ghost layer set to 0).
  *   l2, linf  host pointers (may be NULL).
  */
@@ -230,7 +237,8 @@ int srj_residual(srj_plan_t plan, const double *f, const double *u, double *r_ou
                  double *l2, double *linf, void *stream);
 
 /*
- * srj_boundary_adjoint -- adjoint of the map from Dirichlet data g to b:
+ * srj_boundary_adjoint -- adjoint of the map from Dirichlet data g to b (the
+ * ghost terms of the Sect. 5.1 discretisation; the adjoint is a library feature):
  * for every ghost point q, grad_g[q] = sum of lambda_p over the interior
  * neighbours p of q (b_p = h^2 f_p + sum of ghost neighbours, so dL/dg = B^T
  * dL/db).  lambda and grad_g are device padded float64 arrays; the interior of
@@ -309,7 +317,8 @@ const char *srj_batch_last_error(void);
 
 /*
  * srj_gradient -- backward pass of u = S(f, g), the solution of A_h u = h^2 f + B g
- * (B: ghost neighbours), for a scalar loss L(u).  Given grad_u = dL/du (device,
+ * (B: ghost neighbours; the discretisation of Sect. 5.1, whose A_h is
+ * symmetric), for a scalar loss L(u).  The adjoint is a library feature.  Given grad_u = dL/du (device,
  * padded; its ghost layer is dL/dg through u's own ghost layer, which equals g):
  *   lambda solves A_h lambda = grad_u on the interior (A_h is symmetric, so the
  *   adjoint solve is the same SRJ solve) with lambda = 0 on the ghost layer;
@@ -345,7 +354,9 @@ int srj_schedule_optimal(int P, double kappa_min, double *omega, double *beta, d
  */
 int srj_schedule_for_grid(int ndim, const int64_t *dims, int P, double *omega, int32_t *q, int64_t *M_out);
 
-/* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host). */
+/* kappa_min of a Dirichlet grid with `ndim` axes of dims[i] interior points (host):
+ * (2/d) sum_i sin^2(pi / 2(n_i + 1)), Sect. 5.1 with the normalisation of
+ * Eq. boundaries1D3D. */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 
 /*
@@ -432,22 +443,26 @@ int srj_sph_plan_create(srj_sph_plan_t *plan, int ndim, const int64_t *dims, con
 int srj_sph_plan_destroy(srj_sph_plan_t plan);
 
 /* count FP64 steps of the cycle order from position first (either precision):
- * u (device, in place); writes the active points and row i = 1, leaves the
- * other ghosts as given. */
+ * the weighted-Jacobi step of Sect. 3.1 on the Sect. 5.2 operator, with the
+ * r = 0 and theta prescriptions applied at every step.  u (device, in place);
+ * writes the active points and row i = 1, leaves the other ghosts as given. */
 int srj_sph_steps(srj_sph_plan_t plan, const double *b, double *u, int64_t first, int64_t count, void *stream);
 
-/* l2 / linf (host outputs) of res = L u - b over the active points; r_out
+/* l2 / linf (host outputs) of res = L u - b (the Sect. 5.2 operator) over the
+ * active points; r_out
  * (device, may be NULL) gets res there and 0 elsewhere.  Blocks the host. */
 int srj_sph_residual(srj_sph_plan_t plan, const double *b, const double *u, double *r_out, double *l2,
                      double *linf, void *stream);
 
-/* SRJ cycles until ||res||_2 / ||res_0||_2 <= tol (or max_cycles, divergence,
- * or a stalled residual: stats->stagnated), then the ghost layer and row i = 1
- * are set from the prescriptions.  b, u: device; u in place.  Blocks the host. */
+/* SRJ cycles (Sect. 2) on the Sect. 5.2 operator until ||res||_2 / ||res_0||_2
+ * <= tol (or max_cycles, divergence, or a stalled residual: stats->stagnated),
+ * then the ghost layer and row i = 1 are set from the prescriptions.  b, u:
+ * device; u in place.  Blocks the host. */
 int srj_sph_solve(srj_sph_plan_t plan, const double *b, double *u, double tol, int64_t max_cycles, void *stream,
                   srj_stats_t *stats);
 
-/* Set the ghost layer and row i = 1 of u (device) from the prescriptions. */
+/* Set the ghost layer and row i = 1 of u (device) from the prescriptions of
+ * Sect. 5.2 (u_0 = u_1 = u_2 at r = 0, theta mirrors, periodic phi). */
 int srj_sph_finalize(srj_sph_plan_t plan, double *u, void *stream);
 
 /* FP32 steps per launch of a mixed 2-D spherical plan (1..8; default 8 when
