@@ -19,6 +19,9 @@ M = sum q_i, spectral variable kappa in [kappa_m, kappa_M = 2].
                           of Sect. 3.5.
 * ``solve_optimal``       continuation in P (Sect. 3.3: weights of P+1 levels
                           from the extrapolated extreme weights of P-3..P).
+* ``solve_optimal_fine``  any resolution: below kappa_m = 1e-7 the scheme is
+                          followed from that bound to kappa_m in extended
+                          precision (mpmath, 40 digits; Sect. 3.3 needed 24).
 * ``q_floor``             Sect. 4.3: q_i = floor(beta_i / beta_1).
 * ``rho``                 Eq. rho.
 * ``order_drift``         cycle ordering (Sect. 5.1 asks for the large
@@ -237,6 +240,157 @@ def solve_optimal(P, kappa_m, return_all=False):
             raise ScheduleError("no optimal SRJ scheme found for P=%d, kappa_m=%.6g" % (p, kappa_m))
         hist[p] = found
     return hist if return_all else hist[P]
+
+
+# ---------------------------------------------------------------------------
+# Large grids: extended precision (Sect. 3.3) and continuation in resolution
+# ---------------------------------------------------------------------------
+
+MP_DIGITS = 40          # working precision of the extended-precision stage
+KAPPA_DIRECT = 1.0e-7   # below this bound the double-precision solver is not used directly
+
+
+def system_mp(x, P, kappa_m):
+    """``system`` evaluated in mpmath at the current working precision.
+
+    Sect. 3.3 reports that the optimal schemes for large P and fine grids could
+    only be computed with extended precision (up to 24 digits); the weights then
+    span 1/kappa_m ~ 1e9, and the equations lose that many digits to
+    cancellation.  Same unknowns and equations as ``system``."""
+    import mpmath as mp
+    w = [mp.exp(x[i]) for i in range(P)]
+    inv = [1 / v for v in w]
+    kint = [inv[i] + (inv[i + 1] - inv[i]) / (1 + mp.exp(-x[P + i])) for i in range(P - 1)]
+    beta = []
+    for i in range(P):
+        v = mp.mpf(1)
+        for kk in kint:
+            v *= 1 - kk * w[i]
+        for l in range(P):
+            if l != i:
+                v *= w[l] / (w[l] - w[i])
+        beta.append(v)
+    kap = [mp.mpf(kappa_m)] + kint + [mp.mpf(KAPPA_MAX)]
+    a = [[mp.log(abs(1 - w[i] * kap[j])) for j in range(P + 1)] for i in range(P)]
+    F = [mp.fsum(beta[i] * a[i][j] for i in range(P)) for j in range(P + 1)]
+    eq_max = [F[j] - F[0] for j in range(1, P + 1)]
+    Mm = mp.matrix(P + 1, P + 1)
+    for i in range(P):
+        for j in range(P + 1):
+            Mm[i, j] = kap[j] / (1 - w[i] * kap[j])
+    for j in range(P + 1):
+        Mm[P, j] = 1
+    rhs = mp.matrix(P + 1, 1)
+    rhs[P] = 1
+    mu = mp.lu_solve(Mm, rhs)
+    eq_opt = [mp.fsum(mu[j] * (a[i][j] - a[P - 1][j]) for j in range(P + 1)) for i in range(P - 1)]
+    return eq_max + eq_opt
+
+
+def newton_mp(x0, P, kappa_m, tol=1e-28, maxit=25):
+    """Newton's method on ``system_mp`` from x0 (central-difference Jacobian,
+    step halving until the residual norm decreases).  Returns the solution as
+    an mpmath vector, or None."""
+    import mpmath as mp
+    with mp.workdps(MP_DIGITS):
+        x = [mp.mpf(v) for v in x0]
+        n = len(x)
+        R = system_mp(x, P, kappa_m)
+        nr = mp.norm(mp.matrix(R))
+        for _ in range(maxit):
+            if nr < tol:
+                break
+            J = mp.matrix(n, n)
+            for c in range(n):
+                h = mp.mpf(10) ** -15 * max(1, abs(x[c]))
+                xp = list(x); xp[c] += h
+                xm = list(x); xm[c] -= h
+                Rp, Rm = system_mp(xp, P, kappa_m), system_mp(xm, P, kappa_m)
+                for r in range(n):
+                    J[r, c] = (Rp[r] - Rm[r]) / (2 * h)
+            try:
+                d = mp.lu_solve(J, mp.matrix(R))
+            except ZeroDivisionError:
+                return None
+            alpha, moved = mp.mpf(1), False
+            for _ in range(12):
+                xn = [x[i] - alpha * d[i] for i in range(n)]
+                Rn = system_mp(xn, P, kappa_m)
+                nn = mp.norm(mp.matrix(Rn))
+                if nn < nr:
+                    x, R, nr, moved = xn, Rn, nn, True
+                    break
+                alpha /= 2
+            if not moved:
+                break
+        return x if nr < tol else None
+
+
+def _accept_mp(x, P):
+    import mpmath as mp
+    with mp.workdps(MP_DIGITS):
+        w = [mp.exp(x[i]) for i in range(P)]
+        inv = [1 / v for v in w]
+        kint = [inv[i] + (inv[i + 1] - inv[i]) / (1 + mp.exp(-x[P + i])) for i in range(P - 1)]
+        omega = np.array([float(v) for v in w])
+        if not np.all(np.diff(omega) < 0) or omega[-1] <= 0.5:
+            return None
+        beta = []
+        for i in range(P):
+            v = mp.mpf(1)
+            for kk in kint:
+                v *= 1 - kk * w[i]
+            for l in range(P):
+                if l != i:
+                    v *= w[l] / (w[l] - w[i])
+            beta.append(v)
+        beta = np.array([float(v) for v in beta])
+        if not np.all(beta > 0) or abs(beta.sum() - 1.0) > 1e-12:
+            return None
+        return omega, beta, np.array([float(v) for v in kint])
+
+
+def follow_resolution(P, kappa_from, sol_from, kappa_to):
+    """Follow the optimal P-level scheme from spectral bound kappa_from down to
+    kappa_to (a finer grid) in steps of kappa / 2: at each step the unknowns are
+    predicted by linear extrapolation in log kappa from the two previous
+    solutions and corrected by ``newton_mp``.  The paper computes its tables at
+    a sequence of increasing resolutions (Sect. 4.2); this is that sequence
+    with the previous resolution's solution as the starting point.  Returns
+    (omega, beta, kappa_int) or raises ScheduleError."""
+    import mpmath as mp
+    omega, _, kint = sol_from
+    with mp.workdps(MP_DIGITS):
+        x_cur = [mp.mpf(v) for v in _pack(omega, kint)]
+        x_prev, k_prev, k_cur = None, None, kappa_from
+        ratio = 0.5
+        found = None
+        while k_cur > kappa_to:
+            k_next = max(kappa_to, k_cur * ratio)
+            if x_prev is None:
+                guess = x_cur
+            else:
+                a = mp.log(mp.mpf(k_next) / k_cur) / mp.log(mp.mpf(k_cur) / k_prev)
+                guess = [x_cur[i] + (x_cur[i] - x_prev[i]) * a for i in range(len(x_cur))]
+            x = newton_mp(guess, P, k_next)
+            sol = None if x is None else _accept_mp(x, P)
+            if sol is None:
+                ratio = math.sqrt(ratio)
+                if ratio > 0.97:
+                    raise ScheduleError("optimal P=%d scheme lost at kappa_m=%.6g" % (P, k_next))
+                continue
+            x_prev, x_cur, k_prev, k_cur, found = x_cur, x, k_cur, k_next, sol
+            ratio = 0.5
+    return found
+
+
+def solve_optimal_fine(P, kappa_m):
+    """``solve_optimal`` for any kappa_m: directly when kappa_m >= KAPPA_DIRECT,
+    else solved at KAPPA_DIRECT and followed to kappa_m by
+    ``follow_resolution`` in extended precision."""
+    if kappa_m >= KAPPA_DIRECT:
+        return solve_optimal(P, kappa_m)
+    return follow_resolution(P, KAPPA_DIRECT, solve_optimal(P, KAPPA_DIRECT), kappa_m)
 
 
 def polish(P, kappa_m, omega):

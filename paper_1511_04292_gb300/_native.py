@@ -18,6 +18,9 @@ _BUILD = _PKG / "_build"
 LIB_PATH = _BUILD / "libsrj.so"
 SOURCES = ["srj_kernels.cu", "srj_tblock.cu", "srj_tblock3.cu", "srj_sph.cu", "srj_plan.cu", "srj_batch.cu", "srj_schedule.cu", "srj_noalloc.cu"]
 HEADERS = ["srj_internal.h"]
+# host code whose double-double arithmetic relies on explicit roundings: no
+# floating-point contraction, so that x86-64 and aarch64 builds agree bit for bit
+NO_CONTRACT = {"srj_schedule.cu"}
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -48,6 +51,8 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         obj = _BUILD / (s + ".o")
         objs.append(obj)
         cmd = common + ["-c", str(_CSRC / s), "-o", str(obj)]
+        if s in NO_CONTRACT:
+            cmd += ["-Xcompiler", "-ffp-contract=off"]
         if verbose:
             print(" ".join(cmd))
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -136,6 +141,7 @@ SIGNATURES = {
     "srj_sph_finalize": (_I, [_VP, _VP, _VP]),
     "srj_sph_plan_set_temporal_depth": (_I, [_VP, _I]),
     "srj_sph_plan_temporal_depth": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "srj_selftest_wait_timeout": (_I, [_I64, _VP]),
     "srj_last_error": (ctypes.c_char_p, []),
     "srj_version": (ctypes.c_char_p, []),
 }
