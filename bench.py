@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--count", type=int, default=4)
     ap.add_argument("--ndim", type=int, default=2, choices=[2, 3], help="kernel-case: grid dimension (n^ndim points)")
     ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
-    ap.add_argument("--variant", type=int, default=None, help="kernel-case f32: blocked sweep variant (0 or 1)")
+    ap.add_argument("--variant", type=int, default=None, help="kernel-case f32: blocked sweep variant (0..3)")
     return ap.parse_args()
 
 
@@ -421,8 +421,8 @@ def run_srj(args):
     achieved = 12.0 * pts / (launch_avg_ms / 1e3) / 1e9
     if tuned_T == 1:
         kname = "k_sweep_f32<2>"
-    elif tuned_variant == 1:
-        kname = "k_sweep_f32_tbp<%d>" % tuned_T
+    elif tuned_variant in (1, 3):
+        kname = "k_sweep_f32_tbq<%d,%d>" % (tuned_T, 16 if tuned_variant == 3 else 8)
     else:
         kname = "k_sweep_f32_tb<%d,%d>" % (tuned_T, 16 if tuned_variant == 2 else 8)
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"],

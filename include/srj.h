@@ -54,8 +54,7 @@ extern "C" {
 #define SRJ_ERR_BAD_SCHEDULE  -2  /* integer scheme does not contract on the grid     */
 #define SRJ_ERR_NOT_CONVERGED -3  /* max_cycles reached before tol                   */
 #define SRJ_ERR_DIVERGED      -4  /* residual not finite, or grew by more than 1e6x   */
-#define SRJ_ERR_TIMEOUT       -5  /* reserved: a bounded device-side wait gave up (no    
-                                     current kernel waits on the device)               */
+#define SRJ_ERR_TIMEOUT       -5  /* a bounded device-side wait gave up (1 s limit)  */
 #define SRJ_ERR_CUDA          -6  /* a CUDA runtime call failed                      */
 #define SRJ_ERR_NO_MEMORY     -7  /* device or host allocation failed                */
 
@@ -136,10 +135,16 @@ int srj_plan_set_temporal_depth(srj_plan_t plan, int T);
 
 /*
  * srj_plan_set_sweep_variant -- blocked FP32 sweep strategy of a 2-D mixed plan:
- * 0 = one thread block of 8 warps per 128 x 64 tile; 1 = persistent blocks (2 per
- * SM) that walk the tiles and prefetch the next tile with cp.async while
- * computing the current one; 2 = one block of 16 warps per 128 x 128 tile (less
- * halo recomputation).  All give the same bits.  Re-captures the cycle graph.
+ * 0 = one thread block of 8 warps per 128 x 64 tile; 1 = persistent blocks of
+ * 8 warps (2 per SM) that walk the 128 x 64 tiles and prefetch the next tile's
+ * rows with bulk copies into shared memory while computing the current one;
+ * 2 = one block of 16 warps per 128 x 128 tile (less halo recomputation);
+ * 3 = persistent blocks of 16 warps (1 per SM) on 128 x 128 tiles with the same
+ * prefetch.  All give the same bits.  Re-captures the cycle graph.  The
+ * prefetching variants bound each wait for a prefetch to 1 s of wall time; a
+ * wait that runs out ends its block, and the next call that reads the plan's
+ * results (srj_solve at a cycle end, srj_steps, srj_plan_autotune) returns
+ * SRJ_ERR_TIMEOUT.
  */
 int srj_plan_set_sweep_variant(srj_plan_t plan, int variant);
 
@@ -390,6 +395,19 @@ int srj_steps_f32_noalloc(int ndim, const int64_t *dims, double h, int64_t count
 
 /* Text of the last error of srj_steps_f32_noalloc on the calling thread. */
 const char *srj_noalloc_last_error(void);
+
+/*
+ * srj_selftest_wait_timeout -- self-test of the bounded device-side waits (a
+ * library service; the paper has no counterpart).  Launches the prefetching
+ * sweep (variant 1) on an internal 64 x 64 grid in a mode that issues no
+ * prefetch copy, so every block's wait on its staging barrier runs out after
+ * limit_us microseconds (1 .. 1e6) of wall time; each block then records the
+ * timeout in a device status word and returns, leaving the CUDA context usable.
+ * Allocates and frees its own small device buffers; blocks until done.
+ * Returns SRJ_ERR_TIMEOUT when the waits ran out and were reported, as
+ * designed; SRJ_OK would mean that no wait ran out (a failed self-test).
+ */
+int srj_selftest_wait_timeout(int64_t limit_us, void *stream);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char *srj_last_error(void);

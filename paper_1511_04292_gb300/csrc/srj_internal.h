@@ -82,13 +82,22 @@ int tb_max_steps();
 cudaError_t tb_prepare();  // kernel attributes (dynamic shared memory)
 // T = steps.T consecutive FP32 steps in one launch: reads ein and the defect
 // rin (pitched float32), writes the interior of eout (eout != ein).
-// warps: 8 (128 x 64 tiles) or 16 (128 x 128 tiles).
+// warps: 8 (128 x 64 tiles) or 16 (128 x 128 tiles).  pf_dist > 0: each block
+// also prefetches into L2 the tile pf_dist blocks further on in launch order.
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
-                                const TbSteps& steps, int warps, cudaStream_t s);
-// Persistent variant: `blocks` blocks walk the tiles, prefetching the next one
-// with cp.async while computing the current one.  Same results bit for bit.
+                                const TbSteps& steps, int warps, cudaStream_t s, int pf_dist = 0);
+// Persistent variant (steps.T >= 2): blocks_per_sm * sms blocks of `warps`
+// warps (8: 128 x 64 tiles, two blocks per SM; 16: 128 x 128 tiles, one block
+// per SM) walk the tiles, prefetching the next tile's rows by bulk copies
+// while computing the current one.  Same results bit for bit.  Each wait on a
+// prefetch is bounded by limit_ns of wall time; a wait that runs out sets
+// *status = kStatusTimeout (device memory) and ends its block.  stall != 0
+// launches the bounded-wait self-test (no copy is issued; every wait runs out).
+constexpr int kStatusTimeout = 1;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,
-                                 const TbSteps& steps, int blocks, cudaStream_t s);
+                                 const TbSteps& steps, int warps, int blocks_per_sm, int sms, int* status,
+                                 cudaStream_t s, uint64_t limit_ns = kWaitLimitNs, int stall = 0);
 
 // 3-D: steps.T = 2 or 3 consecutive FP32 steps in one launch, by persistent
 // blocks (at most `blocks`, one per SM) streaming z segments of 128 x 32 tiles.

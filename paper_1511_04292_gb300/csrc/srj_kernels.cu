@@ -177,21 +177,30 @@ k_sweep_f32(Geom g, const float* __restrict__ ein, float* __restrict__ eout,
         const float4 rr = *reinterpret_cast<const float4*>(r + p);
         const float lf = ein[p - 1];
         const float rt = ein[p + 4];
-        float4 nb;
-        nb.x = ((lf + cc.y) + up.x) + dn.x;
-        nb.y = ((cc.x + cc.z) + up.y) + dn.y;
-        nb.z = ((cc.y + cc.w) + up.z) + dn.z;
-        nb.w = ((cc.z + rt) + up.w) + dn.w;
-        if (ND == 3) {
+        // t = sum of the neighbours + defect.  2-D: ((up + down) + r) + (left + right),
+        // the order of the temporally blocked kernels, which form the vertical part
+        // before the horizontal neighbours arrive by warp shuffle.  3-D:
+        // ((((left + right) + up) + down) + (back + front)) + r, the order of the
+        // 3-D blocked kernel.
+        float4 t;
+        if (ND == 2) {
+            t.x = ((up.x + dn.x) + rr.x) + (lf + cc.y);
+            t.y = ((up.y + dn.y) + rr.y) + (cc.x + cc.z);
+            t.z = ((up.z + dn.z) + rr.z) + (cc.y + cc.w);
+            t.w = ((up.w + dn.w) + rr.w) + (cc.z + rt);
+        } else {
             const float4 bk = *reinterpret_cast<const float4*>(ein + p - g.plane32);
             const float4 fr = *reinterpret_cast<const float4*>(ein + p + g.plane32);
-            nb.x += bk.x + fr.x; nb.y += bk.y + fr.y; nb.z += bk.z + fr.z; nb.w += bk.w + fr.w;
+            t.x = ((((lf + cc.y) + up.x) + dn.x) + (bk.x + fr.x)) + rr.x;
+            t.y = ((((cc.x + cc.z) + up.y) + dn.y) + (bk.y + fr.y)) + rr.y;
+            t.z = ((((cc.y + cc.w) + up.z) + dn.z) + (bk.z + fr.z)) + rr.z;
+            t.w = ((((cc.z + rt) + up.w) + dn.w) + (bk.w + fr.w)) + rr.w;
         }
         float4 o;
-        o.x = fmaf(c, fmaf(-two_d, cc.x, nb.x + rr.x), cc.x);
-        o.y = fmaf(c, fmaf(-two_d, cc.y, nb.y + rr.y), cc.y);
-        o.z = fmaf(c, fmaf(-two_d, cc.z, nb.z + rr.z), cc.z);
-        o.w = fmaf(c, fmaf(-two_d, cc.w, nb.w + rr.w), cc.w);
+        o.x = fmaf(c, fmaf(-two_d, cc.x, t.x), cc.x);
+        o.y = fmaf(c, fmaf(-two_d, cc.y, t.y), cc.y);
+        o.z = fmaf(c, fmaf(-two_d, cc.z, t.z), cc.z);
+        o.w = fmaf(c, fmaf(-two_d, cc.w, t.w), cc.w);
         if (mask) {  // inactive points keep their value
             const int64_t q = idx64(g, x0 + 1, y, z);
             if (!mask[q]) o.x = cc.x;

@@ -322,14 +322,18 @@ struct srj_plan {
     // mixed workspaces: two FP32 corrections and the FP32 defect
     float *ea = nullptr, *eb = nullptr, *r32 = nullptr;
     srj::NormScratch ns{};
-    double* host_norms = nullptr;  // pinned, 2 doubles
+    int* kstatus = nullptr;  // device status word of the prefetching sweep, inside the ns.result allocation
+    double* host_norms = nullptr;  // pinned: l2, linf, then the device status word (int) in the third slot
 
     // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
     int tdepth = 1;
     double sigma = 0.0;              // diagonal shift: A = (2d + sigma) I - neighbours
     double diag64 = 0.0;             // 2d + sigma
     unsigned char* mask = nullptr;   // plan-owned copy of the activity mask (NULL: all active)
-    int variant = 0;     // blocked sweep: 0 = one block per tile, 1 = persistent with cp.async prefetch
+    // blocked sweep: 0 = one block of 8 warps per 128 x 64 tile; 1 = persistent blocks of 8 warps (two per SM)
+    // with bulk-copy prefetch; 2 = one block of 16 warps per 128 x 128 tile; 3 = persistent blocks of 16 warps
+    // (one per SM) with bulk-copy prefetch; 4 / 5 = variants 0 / 2 with an L2 prefetch of the next wave's tiles
+    int variant = 0;
     int sm_count = 152;
     float* e_final = nullptr;  // buffer holding the correction after one cycle
     double *host_f = nullptr, *host_u = nullptr;  // device staging of srj_solve_host (allocated on first use)
@@ -375,8 +379,12 @@ cudaError_t issue_f32_steps(srj_plan* p, int64_t first, int64_t count, cudaStrea
             srj::TbSteps st{};
             st.T = n;
             for (int t = 0; t < n; ++t) st.c[t] = (float)p->c64[(size_t)((first + k + t) % M)];
-            err = p->variant == 1 ? srj::launch_sweep_f32_tbp(p->g, in, p->r32, out, st, 2 * p->sm_count, s)
-                                  : srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, p->variant == 2 ? 16 : 8, s);
+            const int v = p->variant;
+            const int warps = (v == 2 || v == 3 || v == 5) ? 16 : 8;
+            err = (v == 1 || v == 3) ? srj::launch_sweep_f32_tbp(p->g, in, p->r32, out, st, warps, 16 / warps,
+                                                                 p->sm_count, p->kstatus, s)
+                                     : srj::launch_sweep_f32_tb(p->g, in, p->r32, out, st, warps, s,
+                                                                v >= 4 ? (16 / warps) * p->sm_count : 0);
         }
         std::swap(in, out);
         k += n;
@@ -417,12 +425,31 @@ int check_plan(srj_plan_t p) {
     return SRJ_OK;
 }
 
+// The device status word of the prefetching sweep (0, or kStatusTimeout when a
+// bounded wait ran out); reset to 0 when it is reported.
+int take_kstatus(srj_plan* p, int word, cudaStream_t s) {
+    if (word == 0) return SRJ_OK;
+    SRJ_CUDA(cudaMemsetAsync(p->kstatus, 0, sizeof(int), s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return fail(SRJ_ERR_TIMEOUT, "a bounded wait of the prefetching sweep ran out (%d); the results are incomplete", word);
+}
+
 int read_norms(srj_plan* p, cudaStream_t s, double* l2, double* linf) {
-    SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     *l2 = p->host_norms[0];
     *linf = p->host_norms[1];
-    return SRJ_OK;
+    int word = 0;
+    std::memcpy(&word, p->host_norms + 2, sizeof(int));
+    return take_kstatus(p, word, s);
+}
+
+// Read the device status word alone (after work that leaves no norms).
+int read_kstatus(srj_plan* p, cudaStream_t s) {
+    int* h = reinterpret_cast<int*>(p->host_norms + 2);
+    SRJ_CUDA(cudaMemcpyAsync(h, p->kstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaStreamSynchronize(s));
+    return take_kstatus(p, *h, s);
 }
 
 // Re-capture the cycle graphs (after a change of the temporal depth).
@@ -572,10 +599,12 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
                      cudaMemset(p->r32, 0, by) == cudaSuccess;
     }
     ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 2 * srj::kMaxNormBlocks) &&
-         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 2 * sizeof(double));
+         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 3 * sizeof(double));
     if (!ok) { cudaGetLastError(); return bail(fail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
+    if (ok) p->kstatus = reinterpret_cast<int*>(p->ns.result + 2);
     if (cudaMemset(p->ns.counter, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMallocHost((void**)&p->host_norms, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(p->ns.result, 0, 3 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->host_norms, 3 * sizeof(double)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
         cudaGetLastError();
@@ -650,9 +679,37 @@ int srj_plan_set_operator(srj_plan_t p, double sigma, const unsigned char* mask,
 int srj_plan_set_sweep_variant(srj_plan_t plan, int v) {
     int rc = check_plan(plan);
     if (rc) return rc;
-    if (v < 0 || v > 2) return fail(SRJ_ERR_INVALID_ARG, "sweep variant must be 0, 1 or 2");
+    if (v < 0 || v > 5) return fail(SRJ_ERR_INVALID_ARG, "sweep variant must be in 0..5");
     plan->variant = v;
     return recapture(plan);
+}
+
+int srj_selftest_wait_timeout(int64_t limit_us, void* stream) {
+    if (limit_us < 1 || limit_us > 1000000) return fail(SRJ_ERR_INVALID_ARG, "limit_us must be in 1..1e6");
+    const int64_t dims[2] = {64, 64};
+    const srj::Geom g = srj::make_geom(2, dims);
+    cudaStream_t s = (cudaStream_t)stream;
+    SRJ_CUDA(srj::tb_prepare());
+    float* buf = nullptr;
+    const size_t by = sizeof(float) * (size_t)g.n32;
+    SRJ_CUDA(cudaMalloc((void**)&buf, 3 * by + 256));
+    int* status = reinterpret_cast<int*>(reinterpret_cast<char*>(buf) + 3 * by);
+    int host_status = 0;
+    srj::TbSteps st{};
+    st.T = 2;
+    st.c[0] = st.c[1] = 0.25f;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 3 * by + 256, s);
+    if (e == cudaSuccess)
+        e = srj::launch_sweep_f32_tbp(g, buf, buf + g.n32, buf + 2 * g.n32, st, 8, 2, 4, status, s,
+                                      (uint64_t)limit_us * 1000ull, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    SRJ_CUDA(e);
+    if (host_status == srj::kStatusTimeout)
+        return fail(SRJ_ERR_TIMEOUT, "bounded waits ran out after %lld us and were reported (self-test passed)",
+                    (long long)limit_us);
+    return fail(SRJ_OK, "no bounded wait ran out (status word %d)", host_status);
 }
 
 int srj_plan_sweep_variant(srj_plan_t plan, int* v) {
@@ -672,9 +729,11 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     // candidates (T, variant): the unblocked sweep, then the blocked variants for T = 2..8 (2-D) or T = 2, 3 (3-D)
-    int candT[22] = {1, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8, 2, 3, 4, 5, 6, 7, 8};
-    int candV[22] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2};
-    int ncand = (p->precision == SRJ_PREC_MIXED && !p->mask && p->sigma == 0.0) ? (p->g.nd == 2 ? 22 : 3) : 1;
+    int candT[43], candV[43];
+    for (int i = 0; i < 8; ++i) { candT[i] = i + 1; candV[i] = 0; }
+    for (int v = 1, i = 8; v <= 5; ++v)
+        for (int T = 2; T <= 8; ++T, ++i) { candT[i] = T; candV[i] = v; }
+    int ncand = (p->precision == SRJ_PREC_MIXED && !p->mask && p->sigma == 0.0) ? (p->g.nd == 2 ? 43 : 3) : 1;
     int bestV = p->variant;
     const int64_t steps = std::min<int64_t>(std::max<int64_t>(p->M, 24), 840);  // 840 = lcm(1..8)
     float best = INFINITY;
@@ -704,7 +763,7 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
         if (ms_best < best) { best = ms_best; bestT = candT[ci]; bestV = candV[ci]; }
     }
     p->variant = bestV;
-    SRJ_CUDA(cudaStreamSynchronize(s));
+    if ((rc = read_kstatus(p, s))) return rc;
     if (best_T) *best_T = bestT;
     if (best_us_per_step) *best_us_per_step = best * 1000.f / (float)steps;
     return set_depth(p, bestT);
@@ -767,8 +826,7 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
         SRJ_CUDA(issue_f32_steps(p, first, count, s, &fin));
         SRJ_CUDA(srj::launch_from_f32(p->g, fin, u, s));
     }
-    SRJ_CUDA(cudaStreamSynchronize(s));
-    return SRJ_OK;
+    return read_kstatus(p, s);
 }
 
 static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, double tol, int64_t max_cycles,

@@ -58,24 +58,24 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
         for (int i = 0; i < kBand; ++i) {
             const float4 cur = e[i];
             const float4 dn = (i + 1 < kBand) ? e[i + 1] : below;
+            // Single-step update in FP32x2 form: per component the unblocked
+            // sweep's fmaf(c, fmaf(-4, e, t), e) with
+            // t = ((up + down) + r) + (left + right), same operations, same
+            // order.  The vertical part needs no other lane, so it is formed
+            // while the horizontal neighbours travel by shuffle.  The left +
+            // right sums are scalar adds whose results land directly in the
+            // (x,y) / (z,w) pairs; pairing the misaligned neighbours for a packed
+            // add would cost more register moves than the adds it saves.
+            float2 v0 = __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y));
+            float2 v1 = __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w));
+            v0 = __fadd2_rn(v0, make_float2(rr[i].x, rr[i].y));
+            v1 = __fadd2_rn(v1, make_float2(rr[i].z, rr[i].w));
             // lanes 0 and 31 receive their own values: those columns lie in the
             // stale halo of the tile, so what they compute is never stored
             const float lf = __shfl_up_sync(0xffffffffu, cur.w, 1);
             const float rt = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            // Single-step update in FP32x2 form: per component the unblocked
-            // sweep's fmaf(c, fmaf(-4, e, nb + r), e) with
-            // nb = ((left + right) + up) + down, same operations, same order.  The left + right sums are
-            // scalar adds whose results land directly in the (x,y) / (z,w)
-            // pairs; pairing the misaligned neighbours for a packed add would
-            // cost more register moves than the adds it saves.
-            float2 s0 = make_float2(lf + cur.y, cur.x + cur.z);
-            float2 s1 = make_float2(cur.y + cur.w, cur.z + rt);
-            s0 = __fadd2_rn(s0, make_float2(up.x, up.y));
-            s1 = __fadd2_rn(s1, make_float2(up.z, up.w));
-            s0 = __fadd2_rn(s0, make_float2(dn.x, dn.y));
-            s1 = __fadd2_rn(s1, make_float2(dn.z, dn.w));
-            s0 = __fadd2_rn(s0, make_float2(rr[i].x, rr[i].y));
-            s1 = __fadd2_rn(s1, make_float2(rr[i].z, rr[i].w));
+            const float2 s0 = __fadd2_rn(v0, make_float2(lf + cur.y, cur.x + cur.z));
+            const float2 s1 = __fadd2_rn(v1, make_float2(cur.y + cur.w, cur.z + rt));
             const float2 c0 = make_float2(cur.x, cur.y), c1 = make_float2(cur.z, cur.w);
             const float2 o0 = __ffma2_rn(cv, __ffma2_rn(m4, c0, s0), c0);
             const float2 o1 = __ffma2_rn(cv, __ffma2_rn(m4, c1, s1), c1);
@@ -167,14 +167,42 @@ __device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const 
     }
 }
 
+// L2 prefetch of the rows of e and of the defect that a warp will load for the
+// tile (bx, by): kBand rows of 128 floats from column X0 + 3 (512 bytes, five
+// 128-byte lines at most) per array.  Lane (i, part) covers line `part` of row i.
+template <int T, int SY>
+__device__ __forceinline__ void prefetch_tile_l2(const float* ein, const float* rin, const Geom& g, int bx, int by,
+                                                 int lane, int w) {
+    constexpr int HX = T <= 4 ? 4 : 8;
+    constexpr int TX = kSX - 2 * HX, TY = SY - 2 * T;
+    const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
+    const int64_t y = (int64_t)Y0 + w * kBand + (lane >> 2);
+    const int part = lane & 3;
+    const int64_t rows = g.ny + 2;
+    if (y < 0 || y >= rows) return;
+    const int64_t c = X0 + 3 + part * 32;
+    if (c >= g.p32) return;  // every address stays inside row y of the buffer
+    const int64_t off = y * g.p32 + (c < 0 ? 0 : c);
+    const int64_t off2 = y * g.p32 + X0 + 3 + 127;  // last float of the row segment (fifth line)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ein + off));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(rin + off));
+    if (part == 3 && X0 + 3 + 127 < g.p32) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ein + off2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rin + off2));
+    }
+}
+
 // Single grid, n = T steps per launch.  Same tile as tile_sweep; interior
 // tiles (the vast majority) load and store without bounds checks.  (Kept as its
 // own body: routed through tile_sweep, this form costs the compiler hundreds of
-// bytes of register spills.)
-template <int T, int W>
+// bytes of register spills.)  PF: after issuing its own loads, each block
+// prefetches into L2 the rows of the tile pf_dist blocks further on in launch
+// order (the tile that starts on a multiprocessor when a resident block ends),
+// so that the next wave's loads are served from L2 while this wave computes.
+template <int T, int W, bool PF = false>
 __global__ void __launch_bounds__(W * 32, 16 / W)
 k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
-               TbSteps steps) {
+               TbSteps steps, int pf_dist = 0) {
     constexpr int HX = T <= 4 ? 4 : 8;
     constexpr int SY = W * kBand;
     constexpr int TX = kSX - 2 * HX, TY = SY - 2 * T;
@@ -214,6 +242,11 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
             }
             iny[i] = y >= 1 && y <= g.ny;
         }
+    }
+    if (PF) {
+        const int lin = (int)(blockIdx.y * gridDim.x + blockIdx.x) + pf_dist;
+        if (lin < (int)(gridDim.x * gridDim.y))
+            prefetch_tile_l2<T, SY>(ein, rin, g, lin % (int)gridDim.x, lin / (int)gridDim.x, lane, w);
     }
     bool inx[4];
 #pragma unroll
@@ -258,66 +291,130 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
     }
 }
 
-__device__ inline void cp_async16(void* smem_dst, const void* gsrc, unsigned src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+// ---- bulk-copy prefetch (persistent form) ----------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase `parity` of the barrier to complete, for at most limit_ns
+// nanoseconds of wall time.  Returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+// One-dimensional bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing `bytes` transactions on the barrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 
-// Persistent form: gridDim.x blocks walk the tiles (x fastest); while a block
-// computes one tile, the band rows of its next tile are copied by cp.async into
-// a shared staging area.  Each lane stages exactly the float4s it reads back,
-// so the staging needs no barrier, only the lane's own cp.async wait.
-template <int T>
-__global__ void __launch_bounds__(kWarps * 32, 2)
-k_sweep_f32_tbp(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
-                TbSteps steps, int tiles_x, int ntiles) {
+// Persistent form with a bulk-copy prefetch: gridDim.x blocks (W = 8: two per
+// SM, W = 16: one) walk the tiles (x fastest).  Warp 0 issues the next tile's
+// rows of e and of the defect as one bulk copy per row into a shared staging
+// area while the block computes the current tile, so that a tile's loads
+// overlap the previous tile's steps instead of following them.  Only the part
+// of each row that lies inside the buffer is copied; the rest of the staging
+// area keeps stale values, which only ever reach points outside the interior
+// (held fixed), exactly like the zeros of the direct-load form, so the stored
+// centre is the same bit for bit.
+//
+// Each wait on the staging barrier is bounded (limit_ns of wall time): when it
+// runs out, the block records SRJ_ERR_TIMEOUT in *status, waits once more
+// (bounded) for its copies in flight, and returns.  stall != 0 is a self-test
+// of that path: the block waits on a barrier phase that nothing completes.
+template <int T, int W>
+__global__ void __launch_bounds__(W * 32, 16 / W)
+k_sweep_f32_tbq(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
+                TbSteps steps, int tiles_x, int ntiles, int* __restrict__ status, uint64_t limit_ns, int stall) {
     constexpr int HX = T <= 4 ? 4 : 8;
-    constexpr int TX = kSX - 2 * HX;
-    constexpr int TY = kSY - 2 * T;
-    __shared__ float4 xch[2 * 2 * kWarps * 32];
-    extern __shared__ float4 stage[];  // [2][kSY][32]: e rows, then r rows
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
-    const int64_t rows = (int64_t)(g.ny + 2) * (g.nd == 3 ? (g.nz + 2) : 1);
-    float4* se = stage;
-    float4* sr = stage + kSY * 32;
+    constexpr int SY = W * kBand;
+    constexpr int TX = kSX - 2 * HX, TY = SY - 2 * T;
+    __shared__ float4 xch[2 * 2 * W * 32];
+    __shared__ __align__(8) unsigned long long full_bar;
+    extern __shared__ __align__(128) float4 stage[];  // [SY][32] rows of e, then [SY][32] rows of the defect
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t bar = smem_addr(&full_bar);
+    const uint32_t sbase = smem_addr(stage);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
-    auto prefetch = [&](int tile) {
+    auto issue = [&](int tile) {  // warp 0 only
         const int bx = tile % tiles_x, by = tile / tiles_x;
         const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
-        const int col = X0 + 3 + 4 * lane;  // multiple of 4: each float4 wholly in or out of the buffer
-        const bool colok = col >= 0 && col + 4 <= g.p32;
+        const int col0 = X0 + 3;  // float32 column of the tile's first point: a multiple of 4
+        const int c0 = max(col0, 0), c1 = min(col0 + kSX, (int)g.p32);
+        const int y0 = max(Y0, 0), y1 = min(Y0 + SY, g.ny + 2);
+        const uint32_t bytes = (uint32_t)(c1 - c0) * 4u;
+        if (lane == 0) mbar_arrive_expect_tx(bar, 2u * (uint32_t)(y1 - y0) * bytes);
+        __syncwarp();
+        const uint32_t dcol = (uint32_t)(c0 - col0) * 4u;
 #pragma unroll
-        for (int i = 0; i < kBand; ++i) {
-            const int row = w * kBand + i;
-            const int64_t y = (int64_t)Y0 + row;
-            const bool ok = colok && y >= 0 && y < rows;
-            const int64_t off = ok ? y * g.p32 + col : 0;
-            cp_async16(&se[row * 32 + lane], ein + off, ok ? 16u : 0u);
-            cp_async16(&sr[row * 32 + lane], rin + off, ok ? 16u : 0u);
+        for (int r = lane; r < SY; r += 32) {
+            const int y = Y0 + r;
+            if (y >= y0 && y < y1) {
+                const int64_t off = (int64_t)y * g.p32 + c0;
+                bulk_g2s(sbase + (uint32_t)r * 512u + dcol, ein + off, bytes, bar);
+                bulk_g2s(sbase + (uint32_t)(SY + r) * 512u + dcol, rin + off, bytes, bar);
+            }
         }
-        cp_async_commit();
     };
 
     int tile = blockIdx.x;
-    if (tile < ntiles) prefetch(tile);
-    for (; tile < ntiles; tile += gridDim.x) {
+    if (w == 0 && !stall) issue(tile);
+    uint32_t parity = 0;
+    for (; tile < ntiles; tile += gridDim.x, parity ^= 1u) {
         const int bx = tile % tiles_x, by = tile / tiles_x;
         const int X0 = 1 + TX * bx - HX, Y0 = 1 + TY * by - T;
-        cp_async_wait_all();
+        const bool ok = mbar_wait_bounded(bar, parity, limit_ns);
         float4 e[kBand], rr[kBand];
         bool iny[kBand];
 #pragma unroll
         for (int i = 0; i < kBand; ++i) {
             const int row = w * kBand + i;
-            e[i] = se[row * 32 + lane];
-            rr[i] = sr[row * 32 + lane];
+            e[i] = stage[row * 32 + lane];
+            rr[i] = stage[(SY + row) * 32 + lane];
             const int y = Y0 + row;
             iny[i] = y >= 1 && y <= g.ny;
         }
-        if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
+        // every thread has read the staging area (and the barrier phase) before
+        // warp 0 refills it; the outcome of the waits is uniform over the block
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, kStatusTimeout);
+                mbar_wait_bounded(bar, parity, limit_ns);  // copies still in flight land first
+            }
+            return;
+        }
+        if (w == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
         bool inx[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -325,36 +422,44 @@ k_sweep_f32_tbp(const float* __restrict__ ein, const float* __restrict__ rin, fl
             inx[j] = x >= 1 && x <= g.nx;
         }
         const bool xin = X0 >= 1 && X0 + kSX - 1 <= g.nx;
-        const bool yin = Y0 >= 1 && Y0 + kSY - 1 <= g.ny;
-        if (xin && yin) band_steps<T, false, false>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else if (xin)   band_steps<T, true, false>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else if (yin)   band_steps<T, false, true>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else            band_steps<T, true, true>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        const bool yin = Y0 >= 1 && Y0 + SY - 1 <= g.ny;
+        if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        else            band_steps<T, true, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
         const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
         if (lane >= lane_lo && lane < lane_hi) {
+            if (xin && yin) {
+                float4* po = reinterpret_cast<float4*>(eout + (int64_t)(Y0 + w * kBand) * g.p32 + X0 + 3 + 4 * lane);
+                const int64_t stride = g.p32 / 4;
 #pragma unroll
-            for (int i = 0; i < kBand; ++i) {
-                const int row = w * kBand + i;
-                if (row < T || row >= T + TY) continue;
-                const int y = Y0 + row;
-                if (y < 1 || y > g.ny) continue;
-                const int x = X0 + 4 * lane;
-                float* dst = eout + (int64_t)y * g.p32 + x + 3;
-                if (inx[0] && inx[3]) {
-                    *reinterpret_cast<float4*>(dst) = e[i];
-                } else {
-                    if (inx[0]) dst[0] = e[i].x;
-                    if (inx[1]) dst[1] = e[i].y;
-                    if (inx[2]) dst[2] = e[i].z;
-                    if (inx[3]) dst[3] = e[i].w;
+                for (int i = 0; i < kBand; ++i) {
+                    const int row = w * kBand + i;
+                    if (row >= T && row < T + TY) po[i * stride] = e[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kBand; ++i) {
+                    const int row = w * kBand + i;
+                    if (row < T || row >= T + TY) continue;
+                    const int y = Y0 + row;
+                    if (y < 1 || y > g.ny) continue;
+                    float* dst = eout + (int64_t)y * g.p32 + X0 + 3 + 4 * lane;
+                    if (inx[0] && inx[3]) {
+                        *reinterpret_cast<float4*>(dst) = e[i];
+                    } else {
+                        if (inx[0]) dst[0] = e[i].x;
+                        if (inx[1]) dst[1] = e[i].y;
+                        if (inx[2]) dst[2] = e[i].z;
+                        if (inx[3]) dst[3] = e[i].w;
+                    }
                 }
             }
         }
         // the next tile's first exchange must not overwrite a slot a slower
-        // warp is still reading in this tile's last step
-        __syncthreads();
+        // warp is still reading in this tile's last step (odd T)
+        if (T & 1) __syncthreads();
     }
-    cp_async_wait_all();
 }
 
 // Batched form: one launch covers the tiles of every problem of a batch; each
@@ -579,37 +684,55 @@ size_t smem_bytes() { return 0; }
 
 int tb_max_steps() { return 8; }
 
-constexpr size_t kStageBytes = 2 * kSY * 32 * sizeof(float4);  // 64 KB
+template <int W>
+constexpr size_t stage_bytes() { return 2 * (size_t)W * kBand * 32 * sizeof(float4); }  // W = 8: 64 KB
 
-template <int T>
+template <int T, int W>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_sweep_f32_tbp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    return cudaFuncSetAttribute(k_sweep_f32_tbq<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_bytes<W>());
 }
 
-template <int T>
+template <int T, int W>
 void launch_P(unsigned grid, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
-              const TbSteps& st, int tiles_x, int ntiles) {
-    k_sweep_f32_tbp<T><<<grid, kWarps * 32, kStageBytes, s>>>(ein, rin, eout, g, st, tiles_x, ntiles);
+              const TbSteps& st, int tiles_x, int ntiles, int* status, uint64_t limit_ns, int stall) {
+    k_sweep_f32_tbq<T, W><<<grid, W * 32, stage_bytes<W>(), s>>>(ein, rin, eout, g, st, tiles_x, ntiles, status,
+                                                                  limit_ns, stall);
+}
+
+template <int W>
+void launch_PW(int T, unsigned grid, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
+               const TbSteps& st, int tiles_x, int ntiles, int* status, uint64_t limit_ns, int stall) {
+    switch (T) {
+        case 2: launch_P<2, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        case 3: launch_P<3, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        case 4: launch_P<4, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        case 5: launch_P<5, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        case 6: launch_P<6, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        case 7: launch_P<7, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+        default: launch_P<8, W>(grid, s, ein, rin, eout, g, st, tiles_x, ntiles, status, limit_ns, stall); break;
+    }
 }
 
 template <int T, int W>
 void launch_T(dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
-              const TbSteps& st) {
-    k_sweep_f32_tb<T, W><<<grd, W * 32, smem_bytes(), s>>>(ein, rin, eout, g, st);
+              const TbSteps& st, int pf_dist) {
+    if (pf_dist > 0) k_sweep_f32_tb<T, W, true><<<grd, W * 32, smem_bytes(), s>>>(ein, rin, eout, g, st, pf_dist);
+    else             k_sweep_f32_tb<T, W, false><<<grd, W * 32, smem_bytes(), s>>>(ein, rin, eout, g, st, 0);
 }
 
 template <int W>
 void launch_W(int T, dim3 grd, cudaStream_t s, const float* ein, const float* rin, float* eout, const Geom& g,
-              const TbSteps& st) {
+              const TbSteps& st, int pf_dist) {
     switch (T) {
-        case 1: launch_T<1, W>(grd, s, ein, rin, eout, g, st); break;
-        case 2: launch_T<2, W>(grd, s, ein, rin, eout, g, st); break;
-        case 3: launch_T<3, W>(grd, s, ein, rin, eout, g, st); break;
-        case 4: launch_T<4, W>(grd, s, ein, rin, eout, g, st); break;
-        case 5: launch_T<5, W>(grd, s, ein, rin, eout, g, st); break;
-        case 6: launch_T<6, W>(grd, s, ein, rin, eout, g, st); break;
-        case 7: launch_T<7, W>(grd, s, ein, rin, eout, g, st); break;
-        default: launch_T<8, W>(grd, s, ein, rin, eout, g, st); break;
+        case 1: launch_T<1, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 2: launch_T<2, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 3: launch_T<3, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 4: launch_T<4, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 5: launch_T<5, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 6: launch_T<6, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        case 7: launch_T<7, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
+        default: launch_T<8, W>(grd, s, ein, rin, eout, g, st, pf_dist); break;
     }
 }
 
@@ -631,42 +754,40 @@ cudaError_t tb_prepare() {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    cudaError_t r[8] = {set_attr<1>(), set_attr<2>(), set_attr<3>(), set_attr<4>(),
-                        set_attr<5>(), set_attr<6>(), set_attr<7>(), set_attr<8>()};
+    cudaError_t r[14] = {set_attr<2, 8>(),  set_attr<3, 8>(),  set_attr<4, 8>(),  set_attr<5, 8>(),
+                         set_attr<6, 8>(),  set_attr<7, 8>(),  set_attr<8, 8>(),  set_attr<2, 16>(),
+                         set_attr<3, 16>(), set_attr<4, 16>(), set_attr<5, 16>(), set_attr<6, 16>(),
+                         set_attr<7, 16>(), set_attr<8, 16>()};
     for (cudaError_t x : r) if (x != cudaSuccess) e = x;
     if (e == cudaSuccess) done[dev].store(true, std::memory_order_release);
     return e;
 }
 
 cudaError_t launch_sweep_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout,
-                                const TbSteps& steps, int warps, cudaStream_t s) {
-    if (g.nd != 2 || steps.T < 1 || steps.T > 8 || (warps != 8 && warps != 16)) return cudaErrorInvalidValue;
+                                const TbSteps& steps, int warps, cudaStream_t s, int pf_dist) {
+    if (g.nd != 2 || steps.T < 1 || steps.T > 8 || (warps != 8 && warps != 16) || pf_dist < 0)
+        return cudaErrorInvalidValue;
     const int HX = steps.T <= 4 ? 4 : 8;
     const int TX = kSX - 2 * HX, TY = warps * kBand - 2 * steps.T;
     dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, 1);
-    if (warps == 16) launch_W<16>(steps.T, grd, s, ein, rin, eout, g, steps);
-    else             launch_W<8>(steps.T, grd, s, ein, rin, eout, g, steps);
+    if (warps == 16) launch_W<16>(steps.T, grd, s, ein, rin, eout, g, steps, pf_dist);
+    else             launch_W<8>(steps.T, grd, s, ein, rin, eout, g, steps, pf_dist);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_f32_tbp(const Geom& g, const float* ein, const float* rin, float* eout,
-                                 const TbSteps& steps, int blocks, cudaStream_t s) {
-    if (g.nd != 2 || steps.T < 1 || steps.T > 8 || blocks < 1) return cudaErrorInvalidValue;
+                                 const TbSteps& steps, int warps, int blocks_per_sm, int sms, int* status,
+                                 cudaStream_t s, uint64_t limit_ns, int stall) {
+    if (g.nd != 2 || steps.T < 2 || steps.T > 8 || (warps != 8 && warps != 16) || sms < 1 || blocks_per_sm < 1 ||
+        !status)
+        return cudaErrorInvalidValue;
     const int HX = steps.T <= 4 ? 4 : 8;
-    const int TX = kSX - 2 * HX, TY = kSY - 2 * steps.T;
+    const int TX = kSX - 2 * HX, TY = warps * kBand - 2 * steps.T;
     const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
     const int ntiles = tx * ty;
-    const unsigned grid = (unsigned)std::min(blocks, ntiles);
-    switch (steps.T) {
-        case 1: launch_P<1>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 2: launch_P<2>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 3: launch_P<3>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 4: launch_P<4>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 5: launch_P<5>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 6: launch_P<6>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        case 7: launch_P<7>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-        default: launch_P<8>(grid, s, ein, rin, eout, g, steps, tx, ntiles); break;
-    }
+    const unsigned grid = (unsigned)std::min(blocks_per_sm * sms, ntiles);
+    if (warps == 16) launch_PW<16>(steps.T, grid, s, ein, rin, eout, g, steps, tx, ntiles, status, limit_ns, stall);
+    else             launch_PW<8>(steps.T, grid, s, ein, rin, eout, g, steps, tx, ntiles, status, limit_ns, stall);
     return cudaGetLastError();
 }
 

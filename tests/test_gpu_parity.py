@@ -378,7 +378,7 @@ def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
         plan.set_temporal_depth(1)
         ref = dev(u)
         plan.steps(fd, ref, first, count)
-        for variant in (0, 1, 2):
+        for variant in range(6):
             plan.set_sweep_variant(variant)
             for T in range(2, 9):
                 plan.set_temporal_depth(T)
@@ -408,6 +408,29 @@ def test_blocked_fp32_sweep_3d_bit_identical_to_single_steps(dims):
             got = dev(u)
             plan.steps(fd, got, first, count)
             assert torch.equal(got, ref), (dims, T, count, first)
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """The prefetching sweep's waits are bounded: in the self-test mode no
+    prefetch copy is issued, every wait runs out after the limit, the blocks
+    report it through the device status word and return, and the context stays
+    usable (a plan created afterwards still reproduces the oracle)."""
+    L = srj.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        rc = L.srj_selftest_wait_timeout(20000, stream)
+        assert rc == -5, L.srj_last_error()
+        assert b"self-test passed" in L.srj_last_error()
+    assert L.srj_selftest_wait_timeout(0, stream) == -1
+    dims = (40, 33)
+    omega, q, order = small_schedule(dims)
+    f, u = random_problem(dims, 5)
+    plan = srj.Plan(dims, 1.0 / 41, omega, q, order, "fp64")
+    ud = dev(u)
+    plan.steps(dev(f), ud, 0, len(order))
+    ref = u.copy()
+    oracle.steps(dims, 1.0 / 41, oracle.omega_sequence(omega, order), f, ref)
+    assert np.array_equal(ud.cpu().numpy(), ref)
 
 
 def test_autotune_picks_a_valid_depth_and_solve_still_converges():
