@@ -40,7 +40,7 @@ MAX_CYCLES = 200
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel at
 # this grid size (warm cache, --cache-control none), keyed by (kernel, n).
 # Entries are removed when the kernel changes.
-MEASURED_TRAFFIC = {("k_sweep_f32_tb<8,8>", 4096): 209_068_928}
+MEASURED_TRAFFIC = {}
 
 
 def parse():
@@ -186,32 +186,135 @@ def workload_config(args):
             "l2": "flushed between timed steps (256 MiB write); per-sweep working set ~134 MB ~ L2 size"}
 
 
-def secondary_workloads(stream):
-    """One timed solve each of the 3-D workload and of the batched workload."""
+def _timed(stream, fn):
+    """(result, ms) of fn() between two CUDA events on `stream` (synchronised)."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream); r = fn(); b.record(stream)
+    torch.cuda.synchronize()
+    return r, a.elapsed_time(b)
+
+
+def _hbm_roofline(kernel, bytes_per_launch, launch_us, peaks, note=None):
+    gbs = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    out = {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": gbs / peaks["hbm_gbs"], "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+           "avg_launch_us": launch_us}
+    if note:
+        out["note"] = note
+    return out
+
+
+# Relative tolerance of the adjoint solve of the gradient line: its right-hand
+# side u - u_t is smooth, so its FP64 floor relative to that right-hand side is
+# ~unit roundoff x cond(A) ~ 2e-10 at 2048^2 (the forward solve's is ~1e-12).
+ADJOINT_TOL = 1e-9
+
+# FP64 sweep roof: GB300 runs 2 FP64 operations per clock per SM (1.25 TFLOP/s
+# counting an FMA as 2); the sweep does 9 FP64 add / multiply operations per
+# update (no FMA, the oracle's order), so its ALU roof is 2 x 152 x 2.07e9 / 9.
+FP64_OPS_PER_UPDATE = 9
+
+
+def _fp64_alu_roofline(kernel, updates, seconds, sm_count, sm_mhz):
+    peak = 2.0 * sm_count * sm_mhz * 1e6 / 1e12  # TFLOP/s of non-fused FP64 operations
+    ach = FP64_OPS_PER_UPDATE * updates / seconds / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": "derived: 2 FP64 ops/clock/SM x %d SMs x %.0f MHz" % (sm_count, sm_mhz),
+            "ops_per_update": FP64_OPS_PER_UPDATE}
+
+
+def config1_workload(stream, peaks):
+    """128^2 interior, FP64, manufactured solution, P = 5, tol 1e-10: GPU time to
+    tolerance (FP64 and mixed) and the oracle run to convergence on one core."""
     import numpy as np
+    import torch
+    import oracle
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
+    n = 128
+    dims = (n, n)
+    f_h, _, u0_h = W.manufactured_2d(n)
+    f = torch.from_numpy(f_h).cuda(); u0 = torch.from_numpy(u0_h).cuda(); u = torch.empty_like(u0)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        plan = srj.Plan.from_table(dims, 5, prec)
+        for _ in range(3):
+            u.copy_(u0); plan.solve(f, u, 1e-10, 2000)
+        u.copy_(u0)
+        st, ms = _timed(stream, lambda: plan.solve(f, u, 1e-10, 2000))
+        res[prec] = {"time_to_tol_s": ms / 1e3, "cycles": st["cycles"], "sweeps": st["sweeps"],
+                     "gupdates_per_s": st["sweeps"] * n * n / (ms / 1e3) / 1e9, "final_rel_residual": st["rel_res"]}
+        if prec == "fp64":
+            M = plan.info()["M"]
+            launch_us = st["sweep_ms"] * 1e3 / st["sweeps"]
+            res[prec]["roofline"] = _hbm_roofline(
+                "k_sweep_f64<2>", 24 * n * n, launch_us, peaks,
+                "403 KB working set: L2-resident and launch-latency bound, far from any HBM roof")
+            res[prec]["sweep_kernel"] = "k_sweep_f64<2> (one FP64 step per launch, %d launches per cycle graph)" % M
+    row = srj.schedules.lookup(2, n, 5)
+    seq = oracle.omega_sequence(row["omega"], row["order"])
+    oracle.build()
+    uo = u0_h.copy()
+    t0 = time.perf_counter()
+    so = oracle.solve(dims, 1.0 / (n + 1), seq, f_h, uo, 1e-10, 2000)
+    dt = time.perf_counter() - t0
+    return {"2d_poisson_128x128_P5_fp64_manufactured_tol1e-10": dict(
+        res["fp64"], mixed=res["mixed"],
+        cpu_baseline={"value": dt, "unit": "s to tol (measured)", "cores": 1, "kind": "oracle",
+                      "sample": "full solve to 1e-10: %d cycles, %d sweeps, rel residual %.3g" %
+                                (so["cycles"], so["sweeps"], so["rel"])},
+        speedup_gpu_fp64_vs_oracle=dt / res["fp64"]["time_to_tol_s"])}
+
+
+def workload_3d(stream, peaks):
+    """512^3, 8 Gaussian blobs, P = 12, tol 1e-9: mixed solve (blocked FP32
+    sweeps) and the plain FP64 SRJ comparator (one cycle timed, times the cycles
+    the mixed solve needed: the cycle map is the same in exact arithmetic)."""
     import torch
     import paper_1511_04292_gb300 as srj
     import srj_workloads as W
-    out = {}
-    # 3-D: 512^3 interior, 8 Gaussian blobs, mixed precision, P = 12, tol 1e-9
     n = 512
     f_h, u0_h = W.gaussian_blobs_3d(n, 3)
     f = torch.from_numpy(f_h).cuda(); u0 = torch.from_numpy(u0_h).cuda(); u = torch.empty_like(u0)
     del f_h, u0_h
     plan = srj.Plan.from_table((n, n, n), 12, "mixed")
+    T = plan.temporal_depth()
+    M = plan.info()["M"]
     u.copy_(u0); plan.solve(f, u, 1e-9, 200)  # warm-up
-    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
-    u.copy_(u0); torch.cuda.synchronize()
-    a.record(stream); st = plan.solve(f, u, 1e-9, 200); b.record(stream); torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    out["3d_poisson_512^3_P12_mixed_tol1e-9"] = {
-        "time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * n ** 3 / (ms / 1e3) / 1e9,
-        "cycles": st["cycles"], "final_rel_residual": st["rel_res"], "temporal_depth": plan.temporal_depth(),
-        "sweep_kernel": "k_sweep3_f32_tb2 (2 steps per launch)" if plan.temporal_depth() == 2 else "k_sweep_f32<3>",
-        "effective_gbs_per_step": 12.0 * n ** 3 * st["sweeps"] / (st["sweep_ms"] / 1e3) / 1e9}
-    del f, u0, u, plan
+    u.copy_(u0)
+    st, ms = _timed(stream, lambda: plan.solve(f, u, 1e-9, 200))
+    launches = st["cycles"] * -(-M // T)
+    out = {"time_to_tol_s": ms / 1e3, "gupdates_per_s": st["sweeps"] * n ** 3 / (ms / 1e3) / 1e9,
+           "cycles": st["cycles"], "final_rel_residual": st["rel_res"], "temporal_depth": T,
+           "sweep_kernel": "k_sweep3_f32_tb2 (2 steps per launch)" if T == 2 else
+                           ("k_sweep3_f32_tb3 (3 steps per launch)" if T == 3 else "k_sweep_f32<3>"),
+           "roofline": _hbm_roofline("k_sweep3_f32_tb%d" % T if T > 1 else "k_sweep_f32<3>", 12 * n ** 3,
+                                     st["sweep_ms"] * 1e3 / launches, peaks)}
+    del plan
     torch.cuda.empty_cache()
-    # spherical (Sect. 5.2 operator, axisymmetric r-theta), 1024^2, P = 10, tol 1e-10: mixed, and FP64 beside it
+    p64 = srj.Plan.from_table((n, n, n), 12, "fp64")
+    u.copy_(u0)
+    st64, ms64 = _timed(stream, lambda: p64.solve(f, u, 0.0, 1, raise_on_fail=False))
+    cyc_ms = st64["sweep_ms"]
+    t64 = (ms64 - cyc_ms) / 1e3 + cyc_ms / 1e3 * st["cycles"]
+    out["fp64_comparator"] = {
+        "time_to_tol_s": t64, "kind": "extrapolated: one FP64 cycle timed (%.0f ms), times the %d cycles of the "
+                                      "mixed solve, plus the measured set-up" % (cyc_ms, st["cycles"]),
+        "gupdates_per_s": M * n ** 3 / (cyc_ms / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<3>"}
+    out["speedup_vs_fp64_time_to_tol"] = t64 / (ms / 1e3)
+    del p64, f, u0, u
+    torch.cuda.empty_cache()
+    return {"3d_poisson_512^3_P12_mixed_tol1e-9": out}
+
+
+def spherical_workload(stream, peaks):
+    """Sect. 5.2 operator (axisymmetric r-theta), 1024^2, P = 10, tol 1e-10:
+    mixed (blocked FP32 cycles) with FP64 beside it."""
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
     from paper_1511_04292_gb300 import spherical as sp
     ns = 1024
     b_h, u0_h = W.spherical_problem_2d(ns, 5)
@@ -222,26 +325,33 @@ def secondary_workloads(stream):
     for prec in ("mixed", "fp64"):
         splan = sp.SphericalPlan((ns, ns), row["omega"], row["q"], row["order"], precision=prec)
         us.copy_(us0); splan.solve(bs, us, 1e-10, 400)  # warm-up
-        us.copy_(us0); torch.cuda.synchronize()
-        a.record(stream); st = splan.solve(bs, us, 1e-10, 400); b.record(stream); torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
+        us.copy_(us0)
+        st, ms = _timed(stream, lambda: splan.solve(bs, us, 1e-10, 400))
         res[prec] = dict(time_to_tol_s=ms / 1e3, gupdates_per_s=st["sweeps"] * act / (ms / 1e3) / 1e9,
-                         cycles=st["cycles"], final_rel_residual=st["rel_res"],
-                         effective_gbs_per_step=(12.0 if prec == "mixed" else 24.0) * act * st["sweeps"]
-                         / (st["sweep_ms"] / 1e3) / 1e9)
+                         cycles=st["cycles"], final_rel_residual=st["rel_res"])
         if prec == "mixed":
             T = splan.temporal_depth()
+            launches = st["cycles"] * -(-len(row["order"]) // T)
             res[prec]["temporal_depth"] = T
             res[prec]["sweep_kernel"] = (f"k_sph_tb<{T}> ({T} FP32 steps per launch, FP64 correction)" if T > 1
                                          else "k_sph_sweep_f32<2> (FP32 cycles, FP64 correction)")
+            res[prec]["roofline"] = _hbm_roofline(
+                f"k_sph_tb<{T}>" if T > 1 else "k_sph_sweep_f32<2>", 12 * act, st["sweep_ms"] * 1e3 / launches, peaks,
+                "12.6 MB working set: L2-resident at this size, bound by FP32 issue (ncu summary)")
         del splan
-    out["spherical_2d_1024x1024_P10_mixed_tol1e-10"] = dict(
-        res["mixed"],
-        fp64_comparator=dict(res["fp64"], sweep_kernel="k_sph_sweep<2> (FP64)"),
-        speedup_vs_fp64_time_to_tol=res["fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"])
     del bs, us0, us
     torch.cuda.empty_cache()
-    # adjoint (gradient of L = 1/2 ||u - u_t||^2 w.r.t. f and the Dirichlet data), 2048^2, FP64, P = 10
+    return {"spherical_2d_1024x1024_P10_mixed_tol1e-10": dict(
+        res["mixed"], fp64_comparator=dict(res["fp64"], sweep_kernel="k_sph_sweep<2> (FP64)"),
+        speedup_vs_fp64_time_to_tol=res["fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"])}
+
+
+def adjoint_workload(stream, peaks, sm_count, sm_mhz):
+    """Gradient of L = 1/2 ||u - u_t||^2 w.r.t. f and the Dirichlet data, 2048^2,
+    FP64, P = 10: forward solve and adjoint solve through the autograd Function."""
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
     from paper_1511_04292_gb300.autograd import srj_solve
     na = 2048
     fa_h, ga_h = W.random_smooth_problem_2d(na, 6)
@@ -258,7 +368,7 @@ def secondary_workloads(stream):
     torch.cuda.synchronize()
     ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     ea.record(stream)
-    ua = srj_solve(fa, ga, aplan, 1e-10, 400)
+    ua = srj_solve(fa, ga, aplan, 1e-10, 400, adjoint_tol=ADJOINT_TOL)
     loss = 0.5 * ((ua - ta)[1:-1, 1:-1] ** 2).sum()
     eb.record(stream)
     loss.backward()
@@ -268,24 +378,121 @@ def secondary_workloads(stream):
     fstats = ua.grad_fn.stats
     bstats = ua.grad_fn.adjoint_stats
     upd = (fstats["sweeps"] + bstats["sweeps"]) * na * na
-    out["adjoint_2d_2048x2048_P10_fp64_tol1e-10"] = {
-        "forward_s": fwd_ms / 1e3, "backward_s": bwd_ms / 1e3, "time_s": (fwd_ms + bwd_ms) / 1e3,
-        "gupdates_per_s": upd / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "forward_cycles": fstats["cycles"],
-        "adjoint_cycles": bstats["cycles"], "adjoint_rel_residual": bstats["rel_res"],
-        "sweep_kernel": "k_sweep_f64<2>"}
+    sweep_s = (fstats["sweep_ms"] + bstats["sweep_ms"]) / 1e3
+    out = {"forward_s": fwd_ms / 1e3, "backward_s": bwd_ms / 1e3, "time_s": (fwd_ms + bwd_ms) / 1e3,
+           "gupdates_per_s": upd / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "forward_cycles": fstats["cycles"],
+           "adjoint_cycles": bstats["cycles"], "forward_rel_residual": fstats["rel_res"],
+           "adjoint_rel_residual": bstats["rel_res"], "adjoint_tol": ua.grad_fn.adjoint_tol,
+           "sweep_kernel": "k_sweep_f64<2>",
+           "roofline": _fp64_alu_roofline("k_sweep_f64<2>", upd, sweep_s, sm_count, sm_mhz)}
     del fa, ga, ta, ua, loss, aplan
     torch.cuda.empty_cache()
-    out.update(batched_workload(stream))
-    return out
+    return {"adjoint_2d_2048x2048_P10_fp64_tol1e-10": out}
 
 
-def batched_workload(stream):
-    """One timed solve of the batched workload: 256 problems, n in {64..1024},
-    P in 5..10, mixed precision, tol 1e-10 (after one untimed solve)."""
+def large_grid_workload(stream, peaks, T, variant, steps=512):
+    """Throughput at 2^15 points per dimension (32768^2, up to ~30 GB on the
+    device).  Per-step times come from (time of 2K steps - time of K steps) / K,
+    which removes the FP64 <-> FP32 conversions srj_steps does around its sweeps.
+
+    FP64: the optimal P = 10 scheme of this grid from the library's planner and
+    cycle order; time to tolerance is an estimate, M steps per cycle x the cycle
+    count the worst eigenmode needs (the plan's max cycle factor) x the per-step
+    time.  Mixed precision: the optimal scheme's largest weight (~1.6e8) makes
+    one step amplify the kappa ~ 2 modes by |1 - 2 omega_1| ~ 3e8 > 1 / eps_32,
+    and the plan rejects its cycle order (modelled FP32 cycle noise above the
+    limit); the FP32 blocked sweep is timed on this grid with the scheme of the
+    4096^2 grid instead (coarser-grid parameters remain convergent on finer
+    grids, Sect. 5.1), in the headline's launch configuration."""
+    import math
     import torch
     import paper_1511_04292_gb300 as srj
     import srj_workloads as W
-    a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+    n = 32768
+    dims = (n, n)
+    f, u0 = W.random_smooth_problem_2d_device(n, 2)
+    u = torch.empty_like(u0)
+
+    def per_step_ms(p, k):
+        u.copy_(u0); p.steps(f, u, 0, k)  # warm-up
+        u.copy_(u0); _, m1 = _timed(stream, lambda: p.steps(f, u, 0, k))
+        u.copy_(u0); _, m2 = _timed(stream, lambda: p.steps(f, u, 0, 2 * k))
+        return (m2 - m1) / k
+
+    out = {"grid": [n, n], "inputs": "f and g from srj_workloads.random_smooth_problem_2d_device (seed 2), "
+                                      "generated on the device"}
+    t0 = time.perf_counter()
+    omega, q = srj.schedules.for_grid(dims, 10)
+    out["planner_s"] = time.perf_counter() - t0
+    M = int(q.sum())
+    kmin, kmax = srj.kappa_range(dims)
+    g10 = srj.schedule_check(omega, q, kmin, kmax)
+    cycles_bound = math.ceil(10.0 / -g10)
+    # the FP64 sweep kernel does not depend on the weights: time it on a one-step plan
+    p64 = srj.Plan(dims, 1.0 / (n + 1), [1.0], [1], None, "fp64")
+    ms64 = per_step_ms(p64, 32)
+    out["fp64"] = {"P": 10, "M": M, "omega_1": float(omega[0]), "us_per_step": ms64 * 1e3,
+                   "gupdates_per_s": n * n / (ms64 / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<2>", "steps_timed": 32,
+                   "time_to_tol_s_estimate": ms64 / 1e3 * M * cycles_bound,
+                   "time_to_tol_kind": "estimate: M steps x %d cycles (1e-10 / max cycle factor %.3g) x measured "
+                                       "per-step time" % (cycles_bound, 10 ** g10)}
+    del p64
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    try:
+        srj.Plan(dims, 1.0 / (n + 1), omega, q, None, "mixed")
+        out["mixed_with_optimal_scheme"] = "accepted"
+    except srj.SRJError as e:
+        out["mixed_with_optimal_scheme"] = "rejected: %s" % str(e).split(": ", 2)[-1]
+    out["mixed_check_s"] = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    row = srj.schedules.lookup(2, 4096, 10)
+    p32 = srj.Plan(dims, 1.0 / (n + 1), row["omega"], row["q"], row["order"], "mixed")
+    p32.set_temporal_depth(T)
+    p32.set_sweep_variant(variant)
+    ms32 = per_step_ms(p32, steps)
+    kname = ("k_sweep_f32_tbq<%d,%d>" % (T, 16 if variant == 3 else 8)) if variant in (1, 3) else \
+            ("k_sweep_f32_tb<%d,%d>" % (T, 16 if variant in (2, 5) else 8))
+    out["mixed"] = {"scheme": "4096^2 grid's P = 10 row (M = %d)" % len(row["order"]), "temporal_depth": T,
+                    "sweep_variant": variant, "steps_timed": steps, "us_per_step": ms32 * 1e3,
+                    "gupdates_per_s": n * n / (ms32 / 1e3) / 1e9,
+                    "roofline": _hbm_roofline(kname, 12 * n * n, ms32 * 1e3 * T, peaks)}
+    out["speedup_fp32_vs_fp64_per_step"] = ms64 / ms32
+    del p32, f, u0, u
+    torch.cuda.empty_cache()
+    return {"2d_poisson_32768x32768_P10_throughput": out}
+
+
+def secondary_workloads(stream, peaks, T, variant):
+    """The other configurations: 128^2 FP64, 3-D 512^3, the spherical operator,
+    the adjoint, the batch, and the 2^15-per-dimension throughput line."""
+    import torch
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {}
+    runs = [("config1", lambda: config1_workload(stream, peaks)),
+            ("3d", lambda: workload_3d(stream, peaks)),
+            ("spherical", lambda: spherical_workload(stream, peaks)),
+            ("adjoint", lambda: adjoint_workload(stream, peaks, sm_count, peaks.get("sm_max_mhz", 2070.0))),
+            ("batch", lambda: batched_workload(stream, peaks, comparators=True)),
+            ("2^15", lambda: large_grid_workload(stream, peaks, T, variant))]
+    for name, fn in runs:
+        try:
+            out.update(fn())
+        except Exception as e:  # one failed line must not hide the others
+            out[name + "_error"] = "%s: %s" % (type(e).__name__, e)
+        torch.cuda.empty_cache()
+    return out
+
+
+def batched_workload(stream, peaks=None, comparators=False):
+    """One timed solve of the batched workload: 256 problems, n in {64..1024},
+    P in 5..10, mixed precision, tol 1e-10 (after one untimed solve).  With
+    comparators: the same problems solved one mixed plan at a time (measured),
+    and by plain FP64 plans (each problem's FP64 cycle timed, times the cycles
+    that problem needed in the batch)."""
+    import torch
+    import paper_1511_04292_gb300 as srj
+    import srj_workloads as W
     out = {}
     specs = W.batch_specs()
     probs, fs, u0s = [], [], []
@@ -298,15 +505,42 @@ def batched_workload(stream):
     us = [x.clone() for x in u0s]
     batch.solve(fs, us, 1e-10, 500)  # warm-up
     us = [x.clone() for x in u0s]
-    torch.cuda.synchronize()
-    a.record(stream); stats, dms, rc = batch.solve(fs, us, 1e-10, 500); b.record(stream); torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
+    (stats, dms, rc), ms = _timed(stream, lambda: batch.solve(fs, us, 1e-10, 500))
+    info = batch.info()
+    T = info["temporal_depth"]
     upd = sum(s_["sweeps"] * nn * nn for s_, (nn, _, _) in zip(stats, specs))
-    out["batched_256_problems_n64-1024_P5-10_mixed_tol1e-10"] = {
-        "time_to_tol_s": ms / 1e3, "gupdates_per_s": upd / (ms / 1e3) / 1e9, "status": rc,
-        "max_cycles": max(s_["cycles"] for s_ in stats), "points": sum(nn * nn for nn, _, _ in specs),
-        "temporal_depth": batch.info()["temporal_depth"],
-        "max_final_rel_residual": max(s_["rel_res"] for s_ in stats)}
+    line = {"time_to_tol_s": ms / 1e3, "gupdates_per_s": upd / (ms / 1e3) / 1e9, "status": rc,
+            "max_cycles": max(s_["cycles"] for s_ in stats), "points": sum(nn * nn for nn, _, _ in specs),
+            "temporal_depth": T, "device_ms": dms,
+            "max_final_rel_residual": max(s_["rel_res"] for s_ in stats)}
+    if peaks is not None:
+        # every launched tile moves its problem's e in, r in, e out once per T steps
+        line["roofline"] = _hbm_roofline(
+            "k_batch_sweep_grp<%d>" % T, 12.0 * upd / T, dms * 1e3, peaks,
+            "achieved over the whole batch solve's device time (one launch = the whole solve; the grouped "
+            "sweep is ~92% of it in the ncu launch list)")
+        line["roofline"]["algorithmic_bytes_per_launch"] = 12.0 * upd / T
+    if comparators:
+        one_ms, f64_ms = 0.0, 0.0
+        for (nn, P, seed), pr, f, u0, st in zip(specs, probs, fs, u0s, stats):
+            p = srj.Plan(pr["dims"], pr["h"], pr["omega"], pr["q"], pr["order"], "mixed")
+            p.set_temporal_depth(T)
+            u = u0.clone()
+            _, m = _timed(stream, lambda: p.solve(f, u, 1e-10, 500))
+            one_ms += m
+            del p
+            p64 = srj.Plan(pr["dims"], pr["h"], pr["omega"], pr["q"], pr["order"], "fp64")
+            u = u0.clone()
+            s64, m64 = _timed(stream, lambda: p64.solve(f, u, 0.0, 1, raise_on_fail=False))
+            f64_ms += (m64 - s64["sweep_ms"]) + s64["sweep_ms"] * st["cycles"]
+            del p64
+        line["one_plan_at_a_time"] = {"time_to_tol_s": one_ms / 1e3, "kind": "measured: each problem's mixed solve "
+                                      "(its own plan, same depth), summed"}
+        line["fp64_comparator"] = {"time_to_tol_s": f64_ms / 1e3, "kind": "extrapolated: each problem's FP64 cycle "
+                                   "timed, times the cycles it needed in the batch, plus its measured set-up; summed"}
+        line["speedup_vs_one_plan_at_a_time"] = one_ms / ms
+        line["speedup_vs_fp64_time_to_tol"] = f64_ms / ms
+    out["batched_256_problems_n64-1024_P5-10_mixed_tol1e-10"] = line
     return out
 
 
@@ -472,15 +706,19 @@ def run_srj(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, dt = oracle_sample(args)
+        sweeps_solve = stats[-1]["sweeps"]
         cpu = {"value": g, "unit": "Gupdates/s", "cores": 1, "kind": "oracle",
                "sample": "%d FP64 oracle sweeps of the full %dx%d grid (%.1f s)" % (args.cpu_sweeps, n, n, dt),
-               "host_cores_total": os.cpu_count()}
+               "host_cores_total": os.cpu_count(),
+               "time_to_tol_s_extrapolated": sweeps_solve * pts / (g * 1e9),
+               "time_to_tol_kind": "extrapolated: the oracle's measured per-sweep time x the %d sweeps the GPU "
+                                   "solve needed (FP64 SRJ needs the same cycles in exact arithmetic)" % sweeps_solve}
 
     secondary = None
     if rank == 0 and not args.no_secondary:
         del p64
         torch.cuda.empty_cache()
-        secondary = secondary_workloads(stream)
+        secondary = secondary_workloads(stream, peaks, tuned_T, tuned_variant)
 
     launches_per_step = 2 + stats[-1]["cycles"] * (launches_per_cycle + 2)
     line = {"metric": METRIC, "value": value, "unit": "Gupdates/s", "n_gpus": world, "steps": args.steps,

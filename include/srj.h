@@ -78,10 +78,15 @@ typedef struct srj_stats {
     double  rel_res;         /* res_l2 / r0_l2 (0 if r0_l2 == 0)                   */
     double  sweep_ms;        /* device time of the M-cycle sweep graphs, summed over
                                 cycles (CUDA events on `stream`)                   */
-    int32_t stagnated;       /* 1 if the solve stopped because the residual had not
-                                halved its best value for 4 cycles (floating-point
-                                floor reached before tol); status NOT_CONVERGED  */
+    int32_t stagnated;       /* 1 if the solve stopped at the floating-point floor
+                                before tol: the residual did not halve in a cycle
+                                while within 64 x res_floor, or had not halved its
+                                best value for 4 cycles; status NOT_CONVERGED     */
     int32_t reserved;
+    double  res_floor;       /* rounding floor of res_l2 at the last cycle end: the
+                                unit roundoff 2^-53 times the 2-norm of the sums of
+                                the absolute values of each residual entry's terms
+                                (single-grid plans; 0 where not computed)         */
 } srj_stats_t;
 
 /*
@@ -364,14 +369,27 @@ int srj_schedule_for_grid(int ndim, const int64_t *dims, int P, double *omega, i
  * Eq. boundaries1D3D. */
 int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
 
+/* Spectral range of the Jacobi-normalised Dirichlet operator D^-1 A of a grid
+ * (host): kappa_min as above and kappa_max = (2/d) sum_i cos^2(pi / 2(n_i + 1)),
+ * the exact extremes of its eigenvalues (2/d) sum_i sin^2(m_i pi / 2(n_i + 1)),
+ * m_i = 1..n_i (Sect. 5.1 / Eq. boundaries1D3D; the schedules themselves are
+ * optimised on [kappa_min, 2], Eq. boundaries).  Either output may be NULL. */
+int srj_kappa_range(int ndim, const int64_t *dims, double *kappa_min, double *kappa_max);
+
+/* Effective Neumann resolution of a Dirichlet grid (host), Eq.
+ * effectiveNDirichlet: N_eff = pi / (2 asin(sqrt((2/d) sum_i sin^2(pi / 2N_i)))),
+ * N_i = n_i + 1 zones for n_i interior points -- the N of the paper's tables
+ * (computed for the Neumann model problem) whose schedule suits this grid. */
+int srj_neff(int ndim, const int64_t *dims, double *n_eff);
+
 /*
  * srj_steps_f32_noalloc -- the FP32 sweep of srj_steps without any device
  * allocation.  (The paper has no counterpart: this is a library service.)
  *
  * For callers that cannot allocate device memory when they need a few sweeps:
- * code whose device memory is all owned by its own fixed pool, latency-critical
- * loops in which cudaMalloc / cudaFree would synchronise the device, and code
- * running while a stream is being captured.  Instead of a plan's workspaces the
+ * code whose device memory is all owned by its own fixed pool, and
+ * latency-critical loops in which cudaMalloc / cudaFree would synchronise the
+ * device.  Instead of a plan's workspaces the
  * work buffers live in one static device array of 12 MiB (3 x 2^20 floats) that
  * every GPU loading this library holds until the process exits; grids whose
  * pitched float32 layout needs more than 2^20 floats per buffer (about 1M padded
@@ -384,11 +402,12 @@ int srj_kappa_min(int ndim, const int64_t *dims, double *kappa_min);
  * ghost layer is left untouched.  f, u: device arrays in the padded layout.
  * Blocks until the work on `stream` is done.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All
- * calls share the array, which keeps the last call's contents (each call clears
- * what it reads); calls whose GPU work overlaps race on it.  Errors are
- * reported through srj_noalloc_last_error().
+ * The first call in a device's CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing); a call after that context
+ * was replaced (cudaDeviceReset, then a new context) looks it up again.  No call
+ * allocates or frees device memory.  All calls share the array, which keeps the
+ * last call's contents (each call clears what it reads); calls whose GPU work
+ * overlaps race on it.  Errors are reported through srj_noalloc_last_error().
  */
 int srj_steps_f32_noalloc(int ndim, const int64_t *dims, double h, int64_t count, const double *omega_seq,
                           const double *f, double *u, void *stream);

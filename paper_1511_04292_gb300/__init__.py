@@ -64,6 +64,34 @@ def kappa_min(dims):
     return out.value
 
 
+def schedule_check(omega, q, kappa_min, kappa_max=2.0):
+    """log10 of the largest cycle amplification |Gamma_cycle| of the integer
+    scheme (omega, q) over [kappa_min, kappa_max] (host; < 0 means it contracts)."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    qq = np.ascontiguousarray(q, dtype=np.int32)
+    out = ctypes.c_double()
+    check(lib().srj_schedule_check(len(om), om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   qq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(kappa_min),
+                                   float(kappa_max), ctypes.byref(out)))
+    return out.value
+
+
+def kappa_range(dims):
+    """(kappa_min, kappa_max): extreme eigenvalues of D^-1 A for a Dirichlet grid."""
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    check(lib().srj_kappa_range(len(dims), d, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def neff(dims):
+    """Effective Neumann resolution N_eff of a Dirichlet grid (Eq. effectiveNDirichlet)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    out = ctypes.c_double()
+    check(lib().srj_neff(len(dims), d, ctypes.byref(out)))
+    return out.value
+
+
 class Plan:
     """An SRJ plan: one grid (dims = (nx, ny[, nz]) interior points, spacing h),
     one schedule (omega_i, q_i[, order]) and one precision ("fp64" or "mixed")."""
@@ -142,7 +170,9 @@ class Plan:
         check(self._lib.srj_plan_set_operator(self._h, float(sigma), mp, _stream_ptr(stream)))
 
     def set_sweep_variant(self, v):
-        """0: one block per tile; 1: persistent blocks with cp.async prefetch (2-D mixed plans)."""
+        """Blocked sweep of 2-D mixed plans: 0 / 2 = one block of 8 / 16 warps per tile;
+        1 / 3 = persistent blocks with a bulk-copy prefetch of the next tile;
+        4 / 5 = variants 0 / 2 with an L2 prefetch of the next wave's tiles."""
         check(self._lib.srj_plan_set_sweep_variant(self._h, int(v)))
 
     def sweep_variant(self):

@@ -85,7 +85,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("residual_checks", ctypes.c_int64),
                 ("r0_l2", ctypes.c_double), ("res_l2", ctypes.c_double), ("res_linf", ctypes.c_double),
                 ("rel_res", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("stagnated", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("res_floor", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +120,8 @@ SIGNATURES = {
     "srj_boundary_adjoint": (_I, [_VP, _VP, _VP, _VP]),
     "srj_gradient": (_I, [_VP, _VP, _VP, _VP, _VP, _D, _I64, _VP, ctypes.POINTER(Stats)]),
     "srj_kappa_min": (_I, [_I, _I64P, _DP]),
+    "srj_kappa_range": (_I, [_I, _I64P, _DP, _DP]),
+    "srj_neff": (_I, [_I, _I64P, _DP]),
     "srj_schedule_check": (_I, [_I, _DP, _I32P, _D, _D, _DP]),
     "srj_schedule_order": (_I, [_I, _DP, _I32P, _D, _I32P]),
     "srj_schedule_optimal": (_I, [_I, _D, _DP, _DP, _DP]),

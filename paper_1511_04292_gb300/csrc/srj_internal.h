@@ -29,11 +29,11 @@ struct Geom {
 Geom make_geom(int nd, const int64_t* dims);
 
 // Reduction scratch for the fused residual norms: per-block partial sums and
-// maxima, a completion counter and the final (l2, linf) pair.
+// maxima, a completion counter and the final norms.
 struct NormScratch {
-    double* partials;      // 2 * kMaxNormBlocks doubles
+    double* partials;      // 3 * kMaxNormBlocks doubles: (sum r^2, max |r|) pairs, then sums of a^2
     unsigned int* counter; // zero between launches
-    double* result;        // [0] = ||r||_2, [1] = max |r|
+    double* result;        // [0] = ||r||_2, [1] = max |r|, [2] = rounding floor of ||r||_2
 };
 constexpr int kMaxNormBlocks = 1216;  // 8 blocks per SM on 152 SMs
 

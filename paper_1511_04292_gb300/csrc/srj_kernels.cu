@@ -96,14 +96,28 @@ __device__ inline void block_reduce(double& ss, double& mx, double* sh_ss, doubl
     }
 }
 
+// Block-wide sum into lane 0 of warp 0.
+__device__ inline void block_sum(double& v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+}
+
 template <int ND>
 __global__ void __launch_bounds__(kThreads)
 k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src, double h2,
            double* __restrict__ r64, float* __restrict__ r32, double scale, NormScratch ns, double two_d,
            const unsigned char* __restrict__ mask) {
-    __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32];
+    __shared__ double sh_ss[kThreads / 32], sh_mx[kThreads / 32], sh_fs[kThreads / 32];
     __shared__ bool last;
     double ss = 0.0, mx = 0.0;
+    double fs = 0.0;  // sum of a^2, a = |neighbours| + |h2 src| + 2d |u|: scale of the rounding in r
     const int64_t rows = (int64_t)g.ny * (ND == 3 ? g.nz : 1);
     for (int64_t rr = blockIdx.x; rr < rows; rr += gridDim.x) {
         const int y = (int)(rr % g.ny) + 1;
@@ -129,12 +143,18 @@ k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src,
             if (r32) r32[idx32(g, x, y, z)] = (float)(r * scale);
             ss = fma(r, r, ss);
             mx = fmax(mx, fabs(r));
+            double a = fabs(u[p - 1]) + fabs(u[p + 1]) + fabs(u[p - g.sx64]) + fabs(u[p + g.sx64]);
+            if (ND == 3) a += fabs(u[p - g.sy64]) + fabs(u[p + g.sy64]);
+            a += fabs(h2 * src[p]) + two_d * fabs(uc);
+            fs = fma(a, a, fs);
         }
     }
     block_reduce(ss, mx, sh_ss, sh_mx);
+    block_sum(fs, sh_fs);
     if (threadIdx.x == 0) {
         ns.partials[2 * blockIdx.x] = ss;
         ns.partials[2 * blockIdx.x + 1] = mx;
+        ns.partials[2 * kMaxNormBlocks + blockIdx.x] = fs;
         __threadfence();
         const unsigned done = atomicAdd(ns.counter, 1u);
         last = (done == gridDim.x - 1);
@@ -142,16 +162,22 @@ k_residual(Geom g, const double* __restrict__ u, const double* __restrict__ src,
     __syncthreads();
     if (!last) return;
     __threadfence();
-    ss = 0.0; mx = 0.0;
+    ss = 0.0; mx = 0.0; fs = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         ss += ((volatile double*)ns.partials)[2 * i];
         mx = fmax(mx, ((volatile double*)ns.partials)[2 * i + 1]);
+        fs += ((volatile double*)ns.partials)[2 * kMaxNormBlocks + i];
     }
+    __syncthreads();  // sh_ss / sh_mx / sh_fs are reused below
     block_reduce(ss, mx, sh_ss, sh_mx);
+    block_sum(fs, sh_fs);
     if (threadIdx.x == 0) {
         ns.result[0] = sqrt(ss);
         // fmax drops NaN; a NaN anywhere already makes ss NaN, report it in both
         ns.result[1] = (ss == ss) ? mx : ss;
+        // rounding floor of ||r||_2: the unit roundoff times ||a||_2 (each
+        // residual entry is a sum of terms of total magnitude a)
+        ns.result[2] = 0x1p-53 * sqrt(fs);
         *ns.counter = 0u;
     }
 }

@@ -2,17 +2,18 @@
 //
 // Some callers cannot allocate device memory at the moment they need a few
 // sweeps: code that owns all device memory through its own fixed pool and
-// forbids foreign cudaMalloc calls, latency-critical loops where cudaMalloc /
-// cudaFree would synchronise the device, and code running while a stream is
-// being captured into a CUDA graph.  For them this entry point keeps the FP32
-// sweep's work buffers (two iterates and the FP32 source) in one file-scope
-// device array of fixed size instead of a plan's cudaMalloc'd workspaces.
+// forbids foreign cudaMalloc calls, and latency-critical loops where cudaMalloc /
+// cudaFree would synchronise the device.  For them this entry point keeps the
+// FP32 sweep's work buffers (two iterates and the FP32 source) in one
+// file-scope device array of fixed size instead of a plan's cudaMalloc'd
+// workspaces.
 //
 // The array is part of the library image: every GPU that loads the library
 // holds it (kNoAllocBytes) until the process exits.  Its device address is
-// looked up once per device with cudaGetSymbolAddress, on the first call made
-// on that device; that first call must therefore happen before any stream
-// capture begins.  All calls share the array and it keeps the last call's
+// looked up with cudaGetSymbolAddress on the first call made in a device's
+// CUDA context, and again on the first call after that context has been
+// replaced (cudaDeviceReset and a new context on the same device); that lookup
+// allocates nothing.  All calls share the array and it keeps the last call's
 // contents, so each call clears the parts it uses; calls whose GPU work
 // overlaps (on different streams, or from different host threads) race on it.
 #include "srj_internal.h"
@@ -29,10 +30,39 @@ constexpr int64_t kNoAllocFloats = int64_t(1) << 20;  // 4 MiB per buffer
 constexpr int64_t kNoAllocBytes = 3 * kNoAllocFloats * 4;
 
 static __device__ __align__(256) float g_noalloc_scratch[3 * kNoAllocFloats];
+static_assert(sizeof(g_noalloc_scratch) == kNoAllocBytes, "scratch size");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // id of the context the address belongs to
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// cuCtxGetCurrent / cuCtxGetId, found through the runtime; no link to libcuda).
+// Returns false when the driver does not provide them.
+bool current_context_id(unsigned long long* id) {
+    typedef int (*get_current_t)(void**);
+    typedef int (*get_id_t)(void*, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<get_current_t>(f1);
+            get_id = reinterpret_cast<get_id_t>(f2);
+        }
+        looked_up = true;
+    }
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
 
 thread_local char g_noalloc_err[256];
 
@@ -49,11 +79,14 @@ int scratch_for_current_device(float** out) {
     if (e != cudaSuccess) return noalloc_fail(SRJ_ERR_CUDA, "cudaGetDevice failed", e);
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SRJ_ERR_INVALID_ARG, "device index out of range");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;  // no current context yet: look the address up (which creates it)
+    const bool have_ctx = current_context_id(&ctx);
+    if (!g_scratch_addr[dev] || !have_ctx || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return noalloc_fail(SRJ_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed", e);
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = have_ctx ? ctx : 0;
     }
     *out = static_cast<float*>(g_scratch_addr[dev]);
     return SRJ_OK;

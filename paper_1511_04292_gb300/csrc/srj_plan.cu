@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -46,7 +47,10 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kMaxLevels = 32;
 constexpr int64_t kMaxM = int64_t(1) << 20;
-constexpr double kMaxFP32CycleNoise = 0.05;  // modelled FP32 rounding left by one cycle (fp32_cycle_noise)
+constexpr double kMaxFP32CycleNoise = 0.05;
+// A solve whose residual stops halving within this factor of the rounding floor
+// of the FP64 residual (unit roundoff x ||sum of |terms|||_2) ends at once.
+constexpr double kFloorFactor = 64.0;  // modelled FP32 rounding left by one cycle (fp32_cycle_noise)
 constexpr int kCheckSamples = 20001;
 
 // Largest eigenvalue of D^-1 A on the Dirichlet grid: (2/d) sum_i cos^2(pi / 2(n_i+1)) < 2.
@@ -135,7 +139,8 @@ std::vector<int32_t> drift_order_once(const std::vector<double>& w, const std::v
             if (left[i] == 0) continue;
             double c = 0.0;
             const double* Li = &L[(size_t)i * K];
-            for (int j = 0; j < K; ++j) c = std::max(c, std::fabs(cur[j] + Li[j] - frac * total[j]));
+            // a level whose deviation already reaches the best one cannot win: stop early
+            for (int j = 0; j < K && c < bestc; ++j) c = std::max(c, std::fabs(cur[j] + Li[j] - frac * total[j]));
             if (c < bestc) { bestc = c; best = i; }
         }
         order[(size_t)s] = best;
@@ -200,14 +205,20 @@ std::vector<int32_t> drift_order(const std::vector<double>& w, const std::vector
     int64_t body_M = 0;
     for (int v : body_q) body_M += v;
     if (body_M > 0) {
+        // the four greedy passes are independent: one host thread each
         const int grids[4] = {1000, 2000, 3000, 4000};
+        std::vector<int32_t> o[4];
+        double wg[4], sg[4];
+        std::vector<std::thread> th;
+        for (int g = 0; g < 4; ++g)
+            th.emplace_back([&, g] {
+                o[g] = drift_order_once(w, body_q, kmin, grids[g]);
+                order_growth(w, o[g], kmin, 4001, &wg[g], &sg[g]);
+            });
+        for (auto& t : th) t.join();
         double bw = INFINITY, bs = INFINITY;
-        for (int K : grids) {
-            std::vector<int32_t> o = drift_order_once(w, body_q, kmin, K);
-            double wg, sg;
-            order_growth(w, o, kmin, 4001, &wg, &sg);
-            if (wg < bw || (wg == bw && sg < bs)) { bw = wg; bs = sg; best.swap(o); }
-        }
+        for (int g = 0; g < 4; ++g)
+            if (wg[g] < bw || (wg[g] == bw && sg[g] < bs)) { bw = wg[g]; bs = sg[g]; best = o[g]; }
     }
     for (int t = 0; t < tail; ++t) best.push_back(P - 1);
     return best;
@@ -277,12 +288,19 @@ std::vector<int32_t> fp32_order(const std::vector<double>& w, const std::vector<
         for (size_t t = 0; t < tail0 + (size_t)m; ++t) o.push_back(small);
         return o;
     };
-    std::vector<double> noise;
-    int best = 0;
-    for (int m = 0; m <= 24 && (size_t)m <= pos.size(); m += 2) {
-        noise.push_back(fp32_cycle_noise(w, cand(m), kmin));
-        if (noise.back() < noise[(size_t)best / 2]) best = m;
+    // the candidates' noise models are independent: one host thread each
+    std::vector<int> ms;
+    for (int m = 0; m <= 24 && (size_t)m <= pos.size(); m += 2) ms.push_back(m);
+    std::vector<double> noise(ms.size());
+    {
+        std::vector<std::thread> th;
+        for (size_t c = 0; c < ms.size(); ++c)
+            th.emplace_back([&, c] { noise[c] = fp32_cycle_noise(w, cand(ms[c]), kmin); });
+        for (auto& t : th) t.join();
     }
+    int best = 0;
+    for (size_t c = 0; c < ms.size(); ++c)
+        if (noise[c] < noise[(size_t)best / 2]) best = ms[c];
     while (best > 0 && (size_t)(best + 4) / 2 < noise.size() && noise[(size_t)(best + 4) / 2] > 2.0 * noise[(size_t)best / 2])
         best -= 2;
     return cand(best);
@@ -322,8 +340,8 @@ struct srj_plan {
     // mixed workspaces: two FP32 corrections and the FP32 defect
     float *ea = nullptr, *eb = nullptr, *r32 = nullptr;
     srj::NormScratch ns{};
-    int* kstatus = nullptr;  // device status word of the prefetching sweep, inside the ns.result allocation
-    double* host_norms = nullptr;  // pinned: l2, linf, then the device status word (int) in the third slot
+    int* kstatus = nullptr;  // device status word of the prefetching sweep: ns.result[3]
+    double* host_norms = nullptr;  // pinned: l2, linf, rounding floor, then the device status word (int)
 
     // temporally blocked FP32 sweeps (2-D mixed plans): depth and tensor maps
     int tdepth = 1;
@@ -435,18 +453,18 @@ int take_kstatus(srj_plan* p, int word, cudaStream_t s) {
 }
 
 int read_norms(srj_plan* p, cudaStream_t s, double* l2, double* linf) {
-    SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SRJ_CUDA(cudaMemcpyAsync(p->host_norms, p->ns.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     *l2 = p->host_norms[0];
     *linf = p->host_norms[1];
     int word = 0;
-    std::memcpy(&word, p->host_norms + 2, sizeof(int));
+    std::memcpy(&word, p->host_norms + 3, sizeof(int));
     return take_kstatus(p, word, s);
 }
 
 // Read the device status word alone (after work that leaves no norms).
 int read_kstatus(srj_plan* p, cudaStream_t s) {
-    int* h = reinterpret_cast<int*>(p->host_norms + 2);
+    int* h = reinterpret_cast<int*>(p->host_norms + 3);
     SRJ_CUDA(cudaMemcpyAsync(h, p->kstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     SRJ_CUDA(cudaStreamSynchronize(s));
     return take_kstatus(p, *h, s);
@@ -485,6 +503,22 @@ int srj_kappa_min(int ndim, const int64_t* dims, double* kappa_min) {
     if ((ndim != 2 && ndim != 3) || !dims || !kappa_min) return fail(SRJ_ERR_INVALID_ARG, "bad arguments");
     for (int i = 0; i < ndim; ++i) if (dims[i] < 1) return fail(SRJ_ERR_INVALID_ARG, "dims must be >= 1");
     *kappa_min = kappa_min_of(ndim, dims);
+    return SRJ_OK;
+}
+
+int srj_kappa_range(int ndim, const int64_t* dims, double* kappa_min, double* kappa_max) {
+    if ((ndim != 2 && ndim != 3) || !dims) return fail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < ndim; ++i) if (dims[i] < 1) return fail(SRJ_ERR_INVALID_ARG, "dims must be >= 1");
+    if (kappa_min) *kappa_min = kappa_min_of(ndim, dims);
+    if (kappa_max) *kappa_max = kappa_max_of(ndim, dims);
+    return SRJ_OK;
+}
+
+int srj_neff(int ndim, const int64_t* dims, double* n_eff) {
+    if ((ndim != 2 && ndim != 3) || !dims || !n_eff) return fail(SRJ_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 0; i < ndim; ++i) if (dims[i] < 1) return fail(SRJ_ERR_INVALID_ARG, "dims must be >= 1");
+    // Eq. effectiveNDirichlet with N_i = n_i + 1 zones; the sum is kappa_min
+    *n_eff = M_PI / (2.0 * std::asin(std::sqrt(kappa_min_of(ndim, dims))));
     return SRJ_OK;
 }
 
@@ -598,13 +632,13 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
         if (ok) ok = cudaMemset(p->ea, 0, by) == cudaSuccess && cudaMemset(p->eb, 0, by) == cudaSuccess &&
                      cudaMemset(p->r32, 0, by) == cudaSuccess;
     }
-    ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 2 * srj::kMaxNormBlocks) &&
-         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 3 * sizeof(double));
+    ok = ok && alloc((void**)&p->ns.partials, sizeof(double) * 3 * srj::kMaxNormBlocks) &&
+         alloc((void**)&p->ns.counter, sizeof(unsigned)) && alloc((void**)&p->ns.result, 4 * sizeof(double));
     if (!ok) { cudaGetLastError(); return bail(fail(SRJ_ERR_NO_MEMORY, "device allocation failed")); }
-    if (ok) p->kstatus = reinterpret_cast<int*>(p->ns.result + 2);
+    if (ok) p->kstatus = reinterpret_cast<int*>(p->ns.result + 3);
     if (cudaMemset(p->ns.counter, 0, sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(p->ns.result, 0, 3 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&p->host_norms, 3 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(p->ns.result, 0, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&p->host_norms, 4 * sizeof(double)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
         cudaGetLastError();
@@ -951,7 +985,18 @@ static int solve_impl(srj_plan_t p, const double* f, double h2, double* u, doubl
                 break;
             }
             if (st.rel_res <= tol) { status = SRJ_OK; break; }
-            if (l2 < 0.5 * best) { best = l2; stall = 0; }
+            st.res_floor = p->host_norms[2];
+            const bool halved = l2 < 0.5 * best;
+            if (!halved && l2 <= kFloorFactor * st.res_floor) {
+                // within a small factor of the rounding floor of the FP64 residual, and no
+                // longer halving: further cycles cannot reach tol
+                st.stagnated = 1;
+                status = fail(SRJ_ERR_NOT_CONVERGED,
+                              "residual reached the FP64 rounding floor at rel %.3g after %lld cycles (floor %.3g, tol %.3g)",
+                              st.rel_res, (long long)(c + 1), st.res_floor / st.r0_l2, tol);
+                break;
+            }
+            if (halved) { best = l2; stall = 0; }
             else if (++stall >= 4) {
                 st.stagnated = 1;
                 status = fail(SRJ_ERR_NOT_CONVERGED, "residual stagnated at rel %.3g after %lld cycles (tol %.3g)",

@@ -108,6 +108,43 @@ def random_smooth_problem_2d(n, seed):
     return smooth_random_2d(n, seed), poly_boundary_2d(n, seed + 1)
 
 
+def random_smooth_problem_2d_device(n, seed, device="cuda"):
+    """The 2-D random smooth workload generated on the device, for grids whose
+    host generation would take minutes (32768^2: 8.6 GB per array).  f: i.i.d.
+    N(0,1) from torch's generator seeded `seed` (so not the numbers of
+    smooth_random_2d, the same distribution), 5x5 box mean with zero padding,
+    ghosts 0.  u0: the Dirichlet data of poly_boundary_2d(n, seed + 1) (same
+    coefficients, same values) on the ghost layer, interior 0.  Returns
+    float64 tensors on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f = torch.zeros((n + 2, n + 2), dtype=torch.float64, device=device)
+    z = torch.randn((1, 1, n, n), generator=g, dtype=torch.float64, device=device)
+    f[1:-1, 1:-1] = torch.nn.functional.avg_pool2d(z, 5, stride=1, padding=2, count_include_pad=True)[0, 0]
+    del z
+    rng = np.random.default_rng(seed + 1)
+    x = coords(n)
+    coef = []
+    for a in range(4):
+        for b in range(4 - a):
+            coef.append((a, b, rng.standard_normal()))
+    ring = {"top": (x, np.zeros_like(x)), "bottom": (x, np.ones_like(x)),
+            "left": (np.zeros_like(x), x), "right": (np.ones_like(x), x)}
+    vals = {}
+    for k, (X, Y) in ring.items():
+        gv = np.zeros_like(X)
+        for a, b, c in coef:
+            gv += c * X ** a * Y ** b
+        vals[k] = torch.from_numpy(gv).to(device)
+    u0 = torch.zeros((n + 2, n + 2), dtype=torch.float64, device=device)
+    u0[0, :] = vals["top"]
+    u0[-1, :] = vals["bottom"]
+    u0[:, 0] = vals["left"]
+    u0[:, -1] = vals["right"]
+    return f, u0
+
+
 def smooth_target_2d(n, seed, kmax=4):
     """u_target = sum_{1<=kx,ky<=kmax} a_k sin(kx pi x) sin(ky pi y), a_k ~ N(0,1)/(kx ky)."""
     rng = np.random.default_rng(seed)

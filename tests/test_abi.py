@@ -34,6 +34,37 @@ def test_kappa_min_matches_oracle():
         assert abs(srj.kappa_min(dims) / oracle.kappa_min_dirichlet(dims) - 1) < 1e-14
 
 
+def test_kappa_range_is_the_spectrum_of_the_jacobi_normalised_operator():
+    """kappa_min / kappa_max are the extreme eigenvalues of D^-1 A, computed here
+    from the dense 5-point (7-point) Dirichlet matrix of small grids."""
+    for dims in [(7, 5), (1, 9), (4, 3, 6), (1, 1, 1)]:
+        n = int(np.prod(dims))
+        d = len(dims)
+        A = 2 * d * np.eye(n)
+        idx = np.arange(n).reshape(dims[::-1])
+        for ax in range(d):
+            a = np.take(idx, range(idx.shape[ax] - 1), axis=ax).ravel()
+            b = np.take(idx, range(1, idx.shape[ax]), axis=ax).ravel()
+            A[a, b] = A[b, a] = -1
+        ev = np.linalg.eigvalsh(A / (2 * d))
+        lo, hi = srj.kappa_range(dims)
+        assert abs(lo - ev[0]) < 1e-13 and abs(hi - ev[-1]) < 1e-13, (dims, lo, hi, ev[0], ev[-1])
+        assert lo == srj.kappa_min(dims)
+
+
+def test_neff_reproduces_the_worked_example():
+    """Eq. effectiveNDirichlet, Sect. 5.1: 585 x 280 zones give N_eff = 252.56
+    (tests/golden/paper_schedules.json, worked example), and for squares and
+    cubes of N zones the large-N form of the same equation,
+    sqrt(d/2) / sqrt(sum_i 1/N_i^2) = N / sqrt(2)."""
+    import json
+    ex = json.loads((Path(__file__).parent / "golden" / "paper_schedules.json").read_text())["worked_example"]
+    zones = ex["zones"]
+    assert round(srj.neff([z - 1 for z in zones]), 2) == ex["n_eff"]
+    assert abs(srj.neff((4095, 4095)) / (4096 / np.sqrt(2)) - 1) < 1e-7
+    assert abs(srj.neff((99, 99, 99)) / (100 / np.sqrt(2)) - 1) < 1e-4
+
+
 def _arr(a, t):
     return np.ascontiguousarray(a, dtype=t)
 

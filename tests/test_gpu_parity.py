@@ -281,15 +281,30 @@ def test_solve_host_equals_device_solve(prec):
 
 def test_full_size_workload2_mixed_solve():
     """Workload 2 at full size (4096^2, P = 10, mixed, tol 1e-10) in the launch
-    configuration the benchmark times: the oracle's residual of the returned u
-    is within tolerance, and one FP32 sweep at this size agrees with the oracle
-    on every point within the rounding bound."""
+    configuration the benchmark times (the autotuner's temporal depth and sweep
+    variant, as the benchmark picks them): one full cycle of that configuration
+    gives the bits of single steps, the oracle's residual of the returned u is
+    within tolerance, and one FP32 sweep at this size agrees with the oracle on
+    every point within the rounding bound."""
     n = 4096
     dims = (n, n)
     f, u0 = W.random_smooth_problem_2d(n, 2)
     plan = srj.Plan.from_table(dims, 10, "mixed")
+    T, _ = plan.autotune()
+    V = plan.sweep_variant()
+    M = plan.info()["M"]
+    fd = dev(f)
+    got = dev(u0)
+    plan.steps(fd, got, 0, M)
+    plan.set_temporal_depth(1)
+    ref = dev(u0)
+    plan.steps(fd, ref, 0, M)
+    assert torch.isfinite(ref).all() and torch.equal(got, ref), (T, V)
+    del got, ref
+    plan.set_temporal_depth(T)
+    plan.set_sweep_variant(V)
     ud = dev(u0)
-    st = plan.solve(dev(f), ud, 1e-10, 100)
+    st = plan.solve(fd, ud, 1e-10, 100)
     u = ud.cpu().numpy()
     r0, _ = oracle.residual(dims, plan.h, f, u0)
     l2, _ = oracle.residual(dims, plan.h, f, u)
