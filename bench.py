@@ -40,7 +40,7 @@ MAX_CYCLES = 200
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel at
 # this grid size (warm cache, --cache-control none), keyed by (kernel, n).
 # Entries are removed when the kernel changes.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("k_sweep_f32_tb<8,8>", 4096): 202_967_168}
 
 
 def parse():
@@ -501,7 +501,8 @@ def batched_workload(stream, peaks=None, comparators=False):
         fh, uh = W.random_smooth_problem_2d(nn, seed)
         probs.append(dict(dims=(nn, nn), h=1.0 / (nn + 1), omega=row["omega"], q=row["q"], order=row["order"]))
         fs.append(torch.from_numpy(fh).cuda()); u0s.append(torch.from_numpy(uh).cuda())
-    batch = srj.Batch(probs)
+    tuned_T, tuned_ms = srj.Batch.tune_depth(probs, fs, u0s, 4, 8, stream=stream)
+    batch = srj.Batch(probs, temporal_depth=tuned_T)
     us = [x.clone() for x in u0s]
     batch.solve(fs, us, 1e-10, 500)  # warm-up
     us = [x.clone() for x in u0s]
@@ -511,7 +512,9 @@ def batched_workload(stream, peaks=None, comparators=False):
     upd = sum(s_["sweeps"] * nn * nn for s_, (nn, _, _) in zip(stats, specs))
     line = {"time_to_tol_s": ms / 1e3, "gupdates_per_s": upd / (ms / 1e3) / 1e9, "status": rc,
             "max_cycles": max(s_["cycles"] for s_ in stats), "points": sum(nn * nn for nn, _, _ in specs),
-            "temporal_depth": T, "device_ms": dms,
+            "temporal_depth": T, "depth_tuner": "srj_batch_tune_depth over T = 4..8 (one cycle of every problem "
+                                                "each): T = %d, %.1f ms per cycle" % (tuned_T, tuned_ms),
+            "device_ms": dms,
             "max_final_rel_residual": max(s_["rel_res"] for s_ in stats)}
     if peaks is not None:
         # every launched tile moves its problem's e in, r in, e out once per T steps

@@ -308,6 +308,19 @@ int srj_batch_create(srj_batch_t *batch, int nprob, const srj_batch_problem_t *p
 
 int srj_batch_destroy(srj_batch_t batch);
 
+/*
+ * srj_batch_tune_depth -- temporal depth for a batch of these problems (a
+ * library service; the paper has no counterpart): for T = tmax down to tmin it
+ * builds the batch with depth T and times one cycle of every problem (each
+ * solve started from copies of u, so f and u, device arrays as for
+ * srj_batch_solve, are left unchanged; the copies are allocated and freed
+ * here), keeping the depth with the shortest device time.  best_T: host
+ * output; best_ms_per_cycle: host, may be NULL.  Blocks the host.
+ */
+int srj_batch_tune_depth(int nprob, const srj_batch_problem_t *problems, const double *const *f,
+                         const double *const *u, int tmin, int tmax, void *stream, int *best_T,
+                         double *best_ms_per_cycle);
+
 /* Sizes of a batch (host outputs, each may be NULL). */
 int srj_batch_info(srj_batch_t batch, int64_t *total_points, int64_t *tiles, int *temporal_depth, int64_t *sum_M);
 

@@ -243,23 +243,40 @@ class Batch:
     problems: list of dicts with keys dims=(nx, ny), h, omega, q, order (or None).
     """
 
-    def __init__(self, problems, temporal_depth=0):
+    @staticmethod
+    def _problem_array(problems):
         from ._native import BatchProblem
-        self._lib = lib()
-        self._keep = []
+        keep, shapes = [], []
         arr = (BatchProblem * len(problems))()
-        self.shapes = []
         for i, pr in enumerate(problems):
             nx, ny = (int(v) for v in pr["dims"])
             om = np.ascontiguousarray(pr["omega"], dtype=np.float64)
             qq = np.ascontiguousarray(pr["q"], dtype=np.int32)
             od = None if pr.get("order") is None else np.ascontiguousarray(pr["order"], dtype=np.int32)
-            self._keep += [om, qq, od]
+            keep += [om, qq, od]
             arr[i].nx, arr[i].ny, arr[i].h, arr[i].P = nx, ny, float(pr["h"]), len(om)
             arr[i].omega = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             arr[i].q = qq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
             arr[i].order = None if od is None else od.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-            self.shapes.append((ny + 2, nx + 2))
+            shapes.append((ny + 2, nx + 2))
+        return arr, keep, shapes
+
+    @staticmethod
+    def tune_depth(problems, fs, us, tmin=2, tmax=8, stream=None):
+        """Temporal depth with the shortest one-cycle batch solve (srj_batch_tune_depth);
+        returns (T, ms per cycle).  fs, us are left unchanged."""
+        arr, keep, shapes = Batch._problem_array(problems)
+        n = len(problems)
+        fp = (ctypes.c_void_p * n)(*[_dev_ptr(f, s, "f").value for f, s in zip(fs, shapes)])
+        up = (ctypes.c_void_p * n)(*[_dev_ptr(u, s, "u").value for u, s in zip(us, shapes)])
+        T = ctypes.c_int(); ms = ctypes.c_double()
+        check(lib().srj_batch_tune_depth(n, arr, fp, up, int(tmin), int(tmax), _stream_ptr(stream), ctypes.byref(T),
+                                         ctypes.byref(ms)), "srj_batch_last_error")
+        return T.value, ms.value
+
+    def __init__(self, problems, temporal_depth=0):
+        self._lib = lib()
+        arr, self._keep, self.shapes = Batch._problem_array(problems)
         h = ctypes.c_void_p()
         check(self._lib.srj_batch_create(ctypes.byref(h), len(problems), arr, int(temporal_depth)),
               "srj_batch_last_error")

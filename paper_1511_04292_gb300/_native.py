@@ -134,6 +134,8 @@ SIGNATURES = {
     "srj_batch_solve": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _D, _I64, _VP,
                              ctypes.POINTER(Stats), _DP]),
     "srj_batch_last_error": (ctypes.c_char_p, []),
+    "srj_batch_tune_depth": (_I, [_I, ctypes.POINTER(BatchProblem), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _I,
+                                  _VP, ctypes.POINTER(ctypes.c_int), _DP]),
     "srj_sph_coefficients": (_I, [_I, _I64P, _DP, _DP, _DP]),
     "srj_sph_plan_create": (_I, [ctypes.POINTER(_VP), _I, _I64P, _DP, _DP, _DP, _I, _DP, _I32P, _I32P, _I]),
     "srj_sph_plan_destroy": (_I, [_VP]),

@@ -644,6 +644,55 @@ int srj_batch_create(srj_batch_t* out, int nprob, const srj_batch_problem_t* pr,
     return SRJ_OK;
 }
 
+int srj_batch_tune_depth(int nprob, const srj_batch_problem_t* pr, const double* const* f, const double* const* u,
+                         int tmin, int tmax, void* stream, int* best_T, double* best_ms_per_cycle) {
+    if (!f || !u || !best_T) return bfail(SRJ_ERR_INVALID_ARG, "NULL argument");
+    if (tmin < 1 || tmax > srj::tb_max_steps() || tmin > tmax)
+        return bfail(SRJ_ERR_INVALID_ARG, "depth range must lie in 1..%d", srj::tb_max_steps());
+    if (nprob < 1 || !pr) return bfail(SRJ_ERR_INVALID_ARG, "need at least one problem");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the trial solves overwrite their iterates: run them on copies of u
+    std::vector<double*> uc((size_t)nprob, nullptr);
+    auto free_all = [&] { for (double* x : uc) cudaFree(x); };
+    for (int p = 0; p < nprob; ++p) {
+        if (!f[p] || !u[p]) { free_all(); return bfail(SRJ_ERR_INVALID_ARG, "problem %d: NULL array", p); }
+        const size_t by = sizeof(double) * (size_t)(pr[p].nx + 2) * (size_t)(pr[p].ny + 2);
+        if (cudaMalloc((void**)&uc[p], by) != cudaSuccess) {
+            cudaGetLastError();
+            free_all();
+            return bfail(SRJ_ERR_NO_MEMORY, "copies of the iterates");
+        }
+    }
+    int bestT = 0;
+    double best = INFINITY;
+    for (int T = tmax; T >= tmin; --T) {
+        srj_batch_t b = nullptr;
+        int rc = srj_batch_create(&b, nprob, pr, T);
+        if (rc) { free_all(); return rc; }
+        double ms = INFINITY;
+        for (int rep = 0; rep < 2 && rc == SRJ_OK; ++rep) {  // the first solve captures the phase graph
+            for (int p = 0; p < nprob; ++p) {
+                const size_t by = sizeof(double) * (size_t)(pr[p].nx + 2) * (size_t)(pr[p].ny + 2);
+                if (cudaMemcpyAsync(uc[p], u[p], by, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = SRJ_ERR_CUDA;
+            }
+            double dms = 0.0;
+            if (rc == SRJ_OK) {
+                // one cycle of every problem (tol 0): every phase of the longest cycle runs once
+                rc = srj_batch_solve(b, f, uc.data(), 0.0, 1, stream, nullptr, &dms);
+                if (rc == SRJ_ERR_NOT_CONVERGED) rc = SRJ_OK;
+            }
+            if (rep == 1) ms = dms;
+        }
+        srj_batch_destroy(b);
+        if (rc) { free_all(); return rc; }
+        if (ms < best) { best = ms; bestT = T; }
+    }
+    free_all();
+    *best_T = bestT;
+    if (best_ms_per_cycle) *best_ms_per_cycle = best;
+    return SRJ_OK;
+}
+
 int srj_batch_destroy(srj_batch_t b) {
     if (!b) return SRJ_OK;
     cudaDeviceSynchronize();

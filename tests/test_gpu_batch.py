@@ -164,3 +164,20 @@ def test_repeated_solve_reuses_the_graph_bit_for_bit():
     assert runs[0][1] == runs[1][1] and len({sw for _, sw in runs[0][1]}) > 1
     for a, b in zip(runs[0][0], runs[1][0]):
         assert torch.equal(a, b)
+
+
+def test_depth_tuner_picks_a_valid_depth_and_leaves_the_inputs():
+    """srj_batch_tune_depth times one cycle of every problem for each depth and
+    returns the fastest; the caller's u is untouched (the trial solves run on
+    copies), and a batch built with the tuned depth converges."""
+    specs = [(64, 5, 21), (256, 6, 23), (128, 8, 25), (512, 7, 27)]
+    probs, fs, u0s = zip(*[_problem(*s) for s in specs])
+    fd = [torch.from_numpy(f).cuda() for f in fs]
+    ud = [torch.from_numpy(u).cuda() for u in u0s]
+    T, ms = srj.Batch.tune_depth(list(probs), fd, ud, 4, 8)
+    assert 4 <= T <= 8 and ms > 0
+    for u, u0 in zip(ud, u0s):
+        assert np.array_equal(u.cpu().numpy(), u0)
+    batch = srj.Batch(list(probs), temporal_depth=T)
+    stats, _, rc = batch.solve(fd, ud, 1e-10, 200)
+    assert rc == 0 and batch.info()["temporal_depth"] == T

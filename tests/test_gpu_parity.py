@@ -207,6 +207,12 @@ def test_stagnation_stops_at_the_floating_point_floor():
         st = plan.solve(dev(f), dev(u0), 1e-30, 10000, raise_on_fail=False)
         assert st["status"] == -3 and st["stagnated"] == 1 and st["cycles"] < 200, st
         assert st["rel_res"] < 1e-11
+        # the rounding-floor estimate is reported
+        assert 0 < st["res_floor"] < st["r0_l2"], st
+    # a tolerance just above the floor is met, so the floor rule does not end a solve early
+    plan = srj.Plan.from_table((n, n), 6, "fp64")
+    st = plan.solve(dev(f), dev(u0), 1e-10, 10000)
+    assert st["status"] == 0 and st["rel_res"] <= 1e-10 and st["stagnated"] == 0
 
 
 def test_zero_problem_converges_immediately():
