@@ -80,7 +80,7 @@ typedef struct srj_stats {
                                 cycles (CUDA events on `stream`)                   */
     int32_t stagnated;       /* 1 if the solve stopped at the floating-point floor
                                 before tol: the residual did not halve in a cycle
-                                while within 64 x res_floor, or had not halved its
+                                while within 8 x res_floor, or had not halved its
                                 best value for 4 cycles; status NOT_CONVERGED     */
     int32_t reserved;
     double  res_floor;       /* rounding floor of res_l2 at the last cycle end: the

@@ -273,3 +273,29 @@ def test_integer_scheme_contracts():
     assert S.max_cycle_factor(omega, q, km) < 0
     bad = q.copy(); bad[0] = q[0] * 20
     assert S.max_cycle_factor(omega, bad, km) > 0
+
+
+def test_window_growth_against_brute_force_windows():
+    """Pin of the order metric: the largest growth of a contiguous run of steps
+    and of a cycle suffix, enumerated window by window (every a < b) at every
+    sampled kappa, for a short cycle of a P = 4 scheme in several orders,
+    including one that puts the large weights together."""
+    km = 1e-3
+    omega, beta, _ = S.solve_optimal(4, km)
+    q = S.q_floor(beta)
+    q = np.minimum(q, 6)
+    base = [i for i, c in enumerate(q) for _ in range(int(c))]
+    rng = np.random.default_rng(5)
+    orders = [base, base[::-1], list(rng.permutation(base)), list(S.order_drift(omega, q, km))]
+    samples = 300
+    kap = np.geomspace(km, 2.0, samples)
+    for order in orders:
+        L = np.log10(np.abs(1.0 - np.outer(np.asarray(omega)[np.asarray(order)], kap)))  # M x K
+        M = len(order)
+        wmax, smax = 0.0, -np.inf
+        for a in range(M):
+            for b in range(a + 1, M + 1):
+                wmax = max(wmax, float(L[a:b].sum(axis=0).max()))
+            smax = max(smax, float(L[a:].sum(axis=0).max()))
+        window, suffix = S.window_growth(omega, order, km, samples=samples)
+        assert abs(window - wmax) < 1e-9 and abs(suffix - smax) < 1e-9, (order, window, wmax, suffix, smax)
