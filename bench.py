@@ -211,18 +211,21 @@ def _hbm_roofline(kernel, bytes_per_launch, launch_us, peaks, note=None):
 # ~unit roundoff x cond(A) ~ 2e-10 at 2048^2 (the forward solve's is ~1e-12).
 ADJOINT_TOL = 1e-9
 
-# FP64 sweep roof: GB300 runs 2 FP64 operations per clock per SM (1.25 TFLOP/s
-# counting an FMA as 2); the sweep does 9 FP64 add / multiply operations per
-# update (no FMA, the oracle's order), so its ALU roof is 2 x 152 x 2.07e9 / 9.
-FP64_OPS_PER_UPDATE = 9
+# FP64 sweep roof: GB300 issues 2 FP64 instructions per clock per SM (1.25
+# TFLOP/s counting an FMA as 2 flops).  A 2-D step is 8 FP64 instructions per
+# update in the oracle's order (4 adds, 2 multiplies, a subtract, an add) and 6
+# with fused multiply-adds (4 adds, 2 FMAs), so the ALU roof is
+# 2 x 152 x 2.07e9 / 8 or / 6 updates per second.
+FP64_OPS_PER_UPDATE = {"fp64": 8, "fp64fma": 6}
 
 
-def _fp64_alu_roofline(kernel, updates, seconds, sm_count, sm_mhz):
-    peak = 2.0 * sm_count * sm_mhz * 1e6 / 1e12  # TFLOP/s of non-fused FP64 operations
-    ach = FP64_OPS_PER_UPDATE * updates / seconds / 1e12
+def _fp64_alu_roofline(kernel, updates, seconds, sm_count, sm_mhz, form="fp64fma"):
+    peak = 2.0 * sm_count * sm_mhz * 1e6 / 1e12  # T FP64 instructions per second (an FMA counts once)
+    ops = FP64_OPS_PER_UPDATE[form]
+    ach = ops * updates / seconds / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_source": "derived: 2 FP64 ops/clock/SM x %d SMs x %.0f MHz" % (sm_count, sm_mhz),
-            "ops_per_update": FP64_OPS_PER_UPDATE}
+            "traffic": None, "peak_source": "derived: 2 FP64 instructions/clock/SM x %d SMs x %.0f MHz" % (sm_count, sm_mhz),
+            "ops_per_update": ops, "ops": "FP64 instructions (an FMA counts once)"}
 
 
 def config1_workload(stream, peaks):
@@ -294,7 +297,7 @@ def workload_3d(stream, peaks):
                                      st["sweep_ms"] * 1e3 / launches, peaks)}
     del plan
     torch.cuda.empty_cache()
-    p64 = srj.Plan.from_table((n, n, n), 12, "fp64")
+    p64 = srj.Plan.from_table((n, n, n), 12, "fp64fma")
     u.copy_(u0)
     st64, ms64 = _timed(stream, lambda: p64.solve(f, u, 0.0, 1, raise_on_fail=False))
     cyc_ms = st64["sweep_ms"]
@@ -302,7 +305,7 @@ def workload_3d(stream, peaks):
     out["fp64_comparator"] = {
         "time_to_tol_s": t64, "kind": "extrapolated: one FP64 cycle timed (%.0f ms), times the %d cycles of the "
                                       "mixed solve, plus the measured set-up" % (cyc_ms, st["cycles"]),
-        "gupdates_per_s": M * n ** 3 / (cyc_ms / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<3>"}
+        "gupdates_per_s": M * n ** 3 / (cyc_ms / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<3,fma>"}
     out["speedup_vs_fp64_time_to_tol"] = t64 / (ms / 1e3)
     del p64, f, u0, u
     torch.cuda.empty_cache()
@@ -358,9 +361,9 @@ def adjoint_workload(stream, peaks, sm_count, sm_mhz):
     ta = torch.from_numpy(W.smooth_target_2d(na, 7)).cuda()
     fa = torch.from_numpy(fa_h).cuda().requires_grad_(True)
     ga = torch.from_numpy(ga_h).cuda().requires_grad_(True)
-    aplan = srj.Plan.from_table((na, na), 10, "fp64")
+    aplan = srj.Plan.from_table((na, na), 10, "fp64fma")
     # untimed: the same expression on a 64^2 problem loads PyTorch's own kernels (loss, autograd)
-    wplan = srj.Plan.from_table((64, 64), 5, "fp64")
+    wplan = srj.Plan.from_table((64, 64), 5, "fp64fma")
     wf = torch.zeros(66, 66, dtype=torch.float64, device="cuda", requires_grad=True)
     wg = torch.zeros(66, 66, dtype=torch.float64, device="cuda", requires_grad=True)
     (0.5 * ((srj_solve(wf, wg, wplan, 1e-10, 50) - ta[:66, :66])[1:-1, 1:-1] ** 2).sum()).backward()
@@ -383,8 +386,8 @@ def adjoint_workload(stream, peaks, sm_count, sm_mhz):
            "gupdates_per_s": upd / ((fwd_ms + bwd_ms) / 1e3) / 1e9, "forward_cycles": fstats["cycles"],
            "adjoint_cycles": bstats["cycles"], "forward_rel_residual": fstats["rel_res"],
            "adjoint_rel_residual": bstats["rel_res"], "adjoint_tol": ua.grad_fn.adjoint_tol,
-           "sweep_kernel": "k_sweep_f64<2>",
-           "roofline": _fp64_alu_roofline("k_sweep_f64<2>", upd, sweep_s, sm_count, sm_mhz)}
+           "sweep_kernel": "k_sweep_f64<2,fma> (FP64 steps with fused multiply-adds)",
+           "roofline": _fp64_alu_roofline("k_sweep_f64<2,fma>", upd, sweep_s, sm_count, sm_mhz)}
     del fa, ga, ta, ua, loss, aplan
     torch.cuda.empty_cache()
     return {"adjoint_2d_2048x2048_P10_fp64_tol1e-10": out}
@@ -429,10 +432,10 @@ def large_grid_workload(stream, peaks, T, variant, steps=512):
     g10 = srj.schedule_check(omega, q, kmin, kmax)
     cycles_bound = math.ceil(10.0 / -g10)
     # the FP64 sweep kernel does not depend on the weights: time it on a one-step plan
-    p64 = srj.Plan(dims, 1.0 / (n + 1), [1.0], [1], None, "fp64")
+    p64 = srj.Plan(dims, 1.0 / (n + 1), [1.0], [1], None, "fp64fma")
     ms64 = per_step_ms(p64, 32)
     out["fp64"] = {"P": 10, "M": M, "omega_1": float(omega[0]), "us_per_step": ms64 * 1e3,
-                   "gupdates_per_s": n * n / (ms64 / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<2>", "steps_timed": 32,
+                   "gupdates_per_s": n * n / (ms64 / 1e3) / 1e9, "sweep_kernel": "k_sweep_f64<2,fma>", "steps_timed": 32,
                    "time_to_tol_s_estimate": ms64 / 1e3 * M * cycles_bound,
                    "time_to_tol_kind": "estimate: M steps x %d cycles (1e-10 / max cycle factor %.3g) x measured "
                                        "per-step time" % (cycles_bound, 10 ** g10)}
@@ -532,7 +535,7 @@ def batched_workload(stream, peaks=None, comparators=False):
             _, m = _timed(stream, lambda: p.solve(f, u, 1e-10, 500))
             one_ms += m
             del p
-            p64 = srj.Plan(pr["dims"], pr["h"], pr["omega"], pr["q"], pr["order"], "fp64")
+            p64 = srj.Plan(pr["dims"], pr["h"], pr["omega"], pr["q"], pr["order"], "fp64fma")
             u = u0.clone()
             s64, m64 = _timed(stream, lambda: p64.solve(f, u, 0.0, 1, raise_on_fail=False))
             f64_ms += (m64 - s64["sweep_ms"]) + s64["sweep_ms"] * st["cycles"]
@@ -687,8 +690,9 @@ def run_srj(args):
         e2e_sweeps += st["sweeps"]
     e2e_value = world * e2e_sweeps * pts / (sum(e2e_ms) / 1e3) / 1e9
 
-    # plain FP64 SRJ comparator on the same grid and schedule
-    p64 = srj.Plan.from_table(dims, args.P, "fp64")
+    # plain FP64 SRJ comparator on the same grid and schedule (FP64 steps with fused multiply-adds, the faster
+    # of the two FP64 forms)
+    p64 = srj.Plan.from_table(dims, args.P, "fp64fma")
     u.copy_(u0)
     torch.cuda.synchronize()
     c64 = args.fp64_cycles if args.fp64_cycles > 0 else MAX_CYCLES
@@ -700,7 +704,7 @@ def run_srj(args):
     ms64 = a.elapsed_time(b)
     g64 = st64["sweeps"] * pts / (ms64 / 1e3) / 1e9
     cyc_mixed = stats[-1]["cycles"]
-    fp64 = {"gupdates_per_s": g64, "cycles_timed": st64["cycles"], "ms": ms64,
+    fp64 = {"gupdates_per_s": g64, "cycles_timed": st64["cycles"], "ms": ms64, "sweep_kernel": "k_sweep_f64<2,fma>",
             "sweep_kernel_gbs": 24.0 * pts / (st64["sweep_ms"] / st64["sweeps"] / 1e3) / 1e9,
             "time_to_tol_s": (ms64 / 1e3 if args.fp64_cycles == 0 else ms64 / 1e3 / st64["cycles"] * cyc_mixed),
             "time_to_tol_kind": "measured" if args.fp64_cycles == 0 else

@@ -65,6 +65,11 @@ extern "C" {
 #define SRJ_PREC_MIXED  1  /* FP64 defect correction: each M-cycle runs in FP32 on
                               A e = r (r = b - A u in FP64, e = 0 on the boundary),
                               then u += e in FP64                                   */
+#define SRJ_PREC_FP64_FMA 2 /* all arithmetic in FP64, each step as
+                              fma(c, fma(-2d, u, sum of neighbours + b), u): 6
+                              operations per point instead of 8, iterates within
+                              FP64 rounding of SRJ_PREC_FP64's (not bit for bit);
+                              residuals as SRJ_PREC_FP64                           */
 
 typedef struct srj_plan *srj_plan_t;
 
@@ -105,7 +110,7 @@ typedef struct srj_stats {
  *              the plan picks an order that keeps the running product of the
  *              amplification factors near its straight-line drift (Sect. 5.1
  *              asks only that large over-relaxations be spread out).  Host.
- *   precision  SRJ_PREC_FP64 or SRJ_PREC_MIXED.
+ *   precision  SRJ_PREC_FP64, SRJ_PREC_FP64_FMA or SRJ_PREC_MIXED.
  * The plan checks that the integer scheme contracts on the grid's spectrum,
  * max over kappa in [kappa_min, kappa_max] of |prod_i (1 - omega_i kappa)^q_i| < 1
  * (Sect. 4.3), with kappa_min = (2/d) sum_i sin^2(pi / 2(n_i+1)) and

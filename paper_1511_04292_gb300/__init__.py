@@ -19,11 +19,14 @@ import numpy as np
 from . import schedules
 from ._native import SRJError, Stats, build, check, lib
 
-__all__ = ["Plan", "Batch", "SRJError", "build", "lib", "schedules", "kappa_min", "PREC_FP64", "PREC_MIXED"]
+__all__ = ["Plan", "Batch", "SRJError", "build", "lib", "schedules", "kappa_min", "kappa_range", "neff",
+           "schedule_check", "PREC_FP64", "PREC_MIXED", "PREC_FP64_FMA"]
 
 PREC_FP64 = 0
 PREC_MIXED = 1
-_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED}
+PREC_FP64_FMA = 2
+_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, "fp64fma": PREC_FP64_FMA,
+         PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED, PREC_FP64_FMA: PREC_FP64_FMA}
 
 
 def _stream_ptr(stream):
@@ -94,7 +97,8 @@ def neff(dims):
 
 class Plan:
     """An SRJ plan: one grid (dims = (nx, ny[, nz]) interior points, spacing h),
-    one schedule (omega_i, q_i[, order]) and one precision ("fp64" or "mixed")."""
+    one schedule (omega_i, q_i[, order]) and one precision: "fp64" (oracle's operation
+    order, bit for bit), "fp64fma" (FP64 steps with fused multiply-adds) or "mixed"."""
 
     def __init__(self, dims, h, omega, q, order=None, precision="fp64"):
         self.dims = tuple(int(v) for v in dims)

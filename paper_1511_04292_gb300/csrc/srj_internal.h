@@ -42,12 +42,13 @@ constexpr int kMaxNormBlocks = 1216;  // 8 blocks per SM on 152 SMs
 // b = h2 * f on the interior (float64 padded layout; ghosts of b set to 0).
 cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, double* b, cudaStream_t s);
 
-// One FP64 weighted-Jacobi step, fixed operation order, no FMA.
+// One FP64 weighted-Jacobi step, fixed operation order, no FMA (fused: the
+// update as fma(c, fma(-2d, u, t), u), t = neighbour sum + b).
 //   uout = uin + c * ((sum nbrs(uin) + b) - 2d uin)    (interior only)
 // two_d: the diagonal 2d + sigma of a shifted operator (0 = plain 2d); mask:
 // padded uint8 array, 0 = point held fixed (NULL = all interior points active).
 cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b,
-                             double c, cudaStream_t s, double two_d = 0.0, const unsigned char* mask = nullptr);
+                             double c, cudaStream_t s, double two_d = 0.0, const unsigned char* mask = nullptr, bool fused = false);
 
 // Fused residual r = (h2 * src + sum nbrs(u)) - 2d u on the interior, with L2 /
 // max norms reduced into ns.result.  Optional outputs: r64 (padded float64,

@@ -45,7 +45,7 @@ __global__ void k_scale_source(Geom g, double h2, const double* __restrict__ f, 
 // FP64 sweep, fixed order, no contraction:
 //   s = (((W + E) + S) + N) [+ B) + T];  t = s + b;  d = t - 2d*u;  u' = u + c*d
 // --------------------------------------------------------------------------
-template <int ND>
+template <int ND, bool FMA = false>
 __global__ void __launch_bounds__(kThreads)
 k_sweep_f64(Geom g, const double* __restrict__ uin, double* __restrict__ uout,
             const double* __restrict__ b, double c, double two_d, const unsigned char* __restrict__ mask) {
@@ -66,8 +66,12 @@ k_sweep_f64(Geom g, const double* __restrict__ uin, double* __restrict__ uout,
             s = __dadd_rn(s, uin[p + g.sy64]);
         }
         const double t = __dadd_rn(s, b[p]);
-        const double dd = __dsub_rn(t, __dmul_rn(two_d, uc));
-        uout[p] = __dadd_rn(uc, __dmul_rn(c, dd));
+        if (FMA) {  // 2 fused operations in place of 4
+            uout[p] = fma(c, fma(-two_d, uc, t), uc);
+        } else {
+            const double dd = __dsub_rn(t, __dmul_rn(two_d, uc));
+            uout[p] = __dadd_rn(uc, __dmul_rn(c, dd));
+        }
     }
 }
 
@@ -377,12 +381,17 @@ cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, doubl
 }
 
 cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b, double c,
-                             cudaStream_t s, double two_d, const unsigned char* mask) {
+                             cudaStream_t s, double two_d, const unsigned char* mask, bool fused) {
     if (two_d == 0.0) two_d = 2.0 * g.nd;
     dim3 blk(64, 4, 1);
     dim3 grd((g.nx + 63) / 64, (g.ny + 3) / 4, g.nd == 3 ? (unsigned)std::min(g.nz, 65535) : 1u);
-    if (g.nd == 3) k_sweep_f64<3><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
-    else           k_sweep_f64<2><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+    if (fused) {
+        if (g.nd == 3) k_sweep_f64<3, true><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+        else           k_sweep_f64<2, true><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+    } else {
+        if (g.nd == 3) k_sweep_f64<3><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+        else           k_sweep_f64<2><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
+    }
     return cudaGetLastError();
 }
 

@@ -331,6 +331,7 @@ struct srj_plan {
     int64_t dims[3] = {1, 1, 1};
     double h = 0, h2 = 0;
     int precision = SRJ_PREC_FP64;
+    bool fused64 = false;  // SRJ_PREC_FP64_FMA: FP64 steps with fused multiply-adds
     std::vector<double> omega;
     std::vector<int32_t> q, order;
     int64_t M = 0;
@@ -422,7 +423,7 @@ int capture_cycle(srj_plan* p, int start) {
         for (int64_t k = 0; k < p->M && err == cudaSuccess; ++k) {
             const bool from_a = ((k + start) % 2) == 0;
             err = srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
-                                        p->c64[(size_t)k], p->cap, p->diag64, p->mask);
+                                        p->c64[(size_t)k], p->cap, p->diag64, p->mask, p->fused64);
         }
     } else {
         err = cudaMemsetAsync(p->ea, 0, sizeof(float) * (size_t)p->g.n32, p->cap);
@@ -569,8 +570,10 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
         if (dims[i] < 1 || dims[i] > (int64_t(1) << 30))
             return fail(SRJ_ERR_INVALID_ARG, "dims[%d] = %lld out of range", i, (long long)dims[i]);
     if (!(h > 0.0) || !std::isfinite(h)) return fail(SRJ_ERR_INVALID_ARG, "h must be finite and > 0");
-    if (precision != SRJ_PREC_FP64 && precision != SRJ_PREC_MIXED)
+    if (precision != SRJ_PREC_FP64 && precision != SRJ_PREC_MIXED && precision != SRJ_PREC_FP64_FMA)
         return fail(SRJ_ERR_INVALID_ARG, "unknown precision %d", precision);
+    const bool fused64 = precision == SRJ_PREC_FP64_FMA;
+    if (fused64) precision = SRJ_PREC_FP64;
     int64_t M = 0;
     if (int rc0 = check_levels(P, omega, q, &M)) return rc0;
     if (dims[1] > 262140) return fail(SRJ_ERR_INVALID_ARG, "dims[1] must be <= 262140 (launch grid limit)");
@@ -585,6 +588,7 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
     p->q.assign(q, q + P);
     p->M = M;
     p->precision = precision;
+    p->fused64 = fused64;
     p->h = h;
     p->h2 = h * h;
     for (int i = 0; i < ndim; ++i) p->dims[i] = dims[i];
@@ -787,7 +791,7 @@ int srj_plan_autotune(srj_plan_t p, void* stream, int* best_T, float* best_us_pe
                 for (int64_t k = 0; k < steps; ++k) {
                     const bool a = (k % 2) == 0;
                     SRJ_CUDA(srj::launch_sweep_f64(p->g, a ? p->ua : p->ub, a ? p->ub : p->ua, p->b,
-                                                   p->c64[(size_t)(k % p->M)], s, p->diag64, p->mask));
+                                                   p->c64[(size_t)(k % p->M)], s, p->diag64, p->mask, p->fused64));
                 }
             }
             SRJ_CUDA(cudaEventRecord(p->ev1, s));
@@ -850,7 +854,7 @@ int srj_steps(srj_plan_t p, const double* f, double* u, int64_t first, int64_t c
         for (int64_t k = 0; k < count; ++k) {
             const bool from_a = (k % 2) == 0;
             SRJ_CUDA(srj::launch_sweep_f64(p->g, from_a ? p->ua : p->ub, from_a ? p->ub : p->ua, p->b,
-                                           p->c64[(size_t)((first + k) % M)], s, p->diag64, p->mask));
+                                           p->c64[(size_t)((first + k) % M)], s, p->diag64, p->mask, p->fused64));
         }
         SRJ_CUDA(cudaMemcpyAsync(u, (count % 2) ? p->ub : p->ua, by, cudaMemcpyDeviceToDevice, s));
     } else {

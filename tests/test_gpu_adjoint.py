@@ -39,7 +39,8 @@ def _laplacian(dims):
     return A.toarray()
 
 
-@pytest.mark.parametrize("dims,prec", [((12, 9), "fp64"), ((5, 4, 6), "fp64"), ((12, 9), "mixed")])
+@pytest.mark.parametrize("dims,prec", [((12, 9), "fp64"), ((5, 4, 6), "fp64"), ((12, 9), "mixed"),
+                                       ((12, 9), "fp64fma")])
 def test_gradient_matches_dense_adjoint(dims, prec):
     nd = len(dims)
     shape = tuple(n + 2 for n in reversed(dims))

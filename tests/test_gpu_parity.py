@@ -69,6 +69,36 @@ def test_fp64_sweeps_bit_identical(dims):
         assert np.array_equal(ud.cpu().numpy(), ref), (dims, first, count)
 
 
+@pytest.mark.parametrize("dims", SHAPES_2D + SHAPES_3D)
+def test_fused_fp64_sweeps_within_rounding_of_the_oracle(dims):
+    """SRJ_PREC_FP64_FMA (each step as fma(c, fma(-2d, u, t), u)): after one
+    full cycle and after a few steps the iterates stay within 1e-12 relative
+    (max norm) of the oracle's at equal sweep count; a full solve converges to
+    the same tolerance in the same cycles as the bit-exact FP64 plan."""
+    omega, q, order = small_schedule(dims)
+    seq = oracle.omega_sequence(omega, order)
+    h = 1.0 / (max(dims) + 1)
+    f, u = random_problem(dims, 300 + len(dims))
+    plan = srj.Plan(dims, h, omega, q, order, "fp64fma")
+    for first, count in [(0, 3), (0, len(seq))]:
+        ud = dev(u)
+        plan.steps(dev(f), ud, first, count)
+        ref = u.copy()
+        oracle.steps(dims, h, seq, f, ref, first=first, count=count)
+        got = ud.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (dims, first, count)
+    if min(dims) >= 3:
+        u0 = u.copy(); u0[tuple(slice(1, -1) for _ in dims)] = 0.0
+        exact = srj.Plan(dims, h, omega, q, order, "fp64")
+        st_e = exact.solve(dev(f), dev(u0), 1e-10, 500)
+        ud = dev(u0)
+        st_f = plan.solve(dev(f), ud, 1e-10, 500)
+        assert st_f["cycles"] == st_e["cycles"] and st_f["rel_res"] <= 1e-10
+        r0, _ = oracle.residual(dims, h, f, u0)
+        l2, _ = oracle.residual(dims, h, f, ud.cpu().numpy())
+        assert l2 <= 1e-10 * r0 * (1 + 1e-9)
+
+
 @pytest.mark.parametrize("case", ["2d_4096_P10", "3d_512_P12"])
 def test_full_size_fp64_steps_and_residual_bit_identical(case):
     """The FP64 path at the workloads' full sizes, in the launch configuration of
@@ -497,3 +527,56 @@ def test_auto_plan_from_native_planner_converges():
         r0, _ = oracle.residual(dims, plan.h, f, u0)
         l2, _ = oracle.residual(dims, plan.h, f, ud.cpu().numpy())
         assert l2 <= 1e-10 * r0 * (1 + 1e-9)
+
+
+def test_full_size_2pow15_sweeps():
+    """The 32768^2 throughput line's launch configurations at full size: the
+    blocked FP32 sweep (T = 8, the 4096^2 grid's scheme, as the benchmark runs
+    it) gives the bits of single steps, one FP32 step agrees with the oracle
+    within the rounding bound on sampled rows, and the FP64 sweep is
+    bit-identical to the oracle on sampled rows."""
+    n = 32768
+    dims = (n, n)
+    h = 1.0 / (n + 1)
+    f, u0 = W.random_smooth_problem_2d_device(n, 2)
+    # a nonzero interior, so that every term of the update is exercised
+    u0[1:-1, 1:-1] = 0.25 * f[1:-1, 1:-1]
+    row = srj.schedules.lookup(2, 4096, 10)
+    plan = srj.Plan(dims, h, row["omega"], row["q"], row["order"], "mixed")
+    plan.set_temporal_depth(8)
+    plan.set_sweep_variant(0)
+    first, count = 5, 16
+    got = u0.clone()
+    plan.steps(f, got, first, count)
+    plan.set_temporal_depth(1)
+    ref = u0.clone()
+    plan.steps(f, ref, first, count)
+    assert torch.isfinite(ref).all() and torch.equal(got, ref)
+    del got, ref
+    sample_rows = (1, 2, 48, 49, 12345, n - 1, n)
+    # one FP32 step of the cycle's first weight against the oracle, on 3-row slabs
+    w = float(row["omega"][row["order"][0]])
+    one = u0.clone()
+    plan.steps(f, one, 0, 1)
+    for y in sample_rows:
+        us = u0[y - 1:y + 2].cpu().numpy()
+        fs = f[y - 1:y + 2].cpu().numpy()
+        u32 = us.astype(np.float32).astype(np.float64)
+        f32 = (h * h * fs).astype(np.float32).astype(np.float64) / (h * h)
+        refrow = oracle.sweep((n, 1), h, w, f32, u32)[1]
+        c = w / 4
+        nb = sum(np.abs(np.roll(u32, s, axis=a)) for a in (0, 1) for s in (-1, 1))[1]
+        bound = 8 * 2.0 ** -24 * (np.abs(u32[1]) + c * (nb + np.abs(h * h * f32[1]) + 4 * np.abs(u32[1])))
+        diff = np.abs(one[y].cpu().numpy() - refrow)
+        assert np.all(diff[1:-1] <= bound[1:-1]), (y, float(diff[1:-1].max()))
+    del one, plan
+    torch.cuda.empty_cache()
+    # FP64 sweep (the benchmark times it on a one-weight plan): bit-identical rows
+    p64 = srj.Plan(dims, h, [1.0], [1], None, "fp64")
+    u64 = u0.clone()
+    p64.steps(f, u64, 0, 1)
+    for y in sample_rows:
+        us = u0[y - 1:y + 2].cpu().numpy()
+        fs = f[y - 1:y + 2].cpu().numpy()
+        refrow = oracle.sweep((n, 1), h, 1.0, fs, us)[1]
+        assert np.array_equal(u64[y].cpu().numpy(), refrow), y
