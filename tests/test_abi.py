@@ -171,3 +171,21 @@ def test_batch_argument_checks_before_touching_the_gpu(bad):
     with pytest.raises(srj.SRJError) as ei:
         srj.Batch(probs, temporal_depth=depth)
     assert ei.value.status == (-2 if bad == "contraction" else -1), (bad, str(ei.value))
+
+
+def test_tuner_and_self_test_argument_checks_before_touching_the_gpu():
+    """srj_batch_tune_depth and srj_selftest_wait_timeout reject bad arguments
+    (NULL arrays, an empty or out-of-range depth range, a wait limit outside
+    1 us .. 1 s) with SRJ_ERR_INVALID_ARG before any CUDA call."""
+    L = srj.lib()
+    probs = [dict(dims=(40, 30), h=1 / 41, omega=[2.0, 0.7], q=[1, 3], order=[1, 0, 1, 1])]
+    arr, keep, _ = srj.Batch._problem_array(probs)
+    dummy = (ctypes.c_void_p * 1)(ctypes.c_void_p(0))
+    T = ctypes.c_int()
+    for f, u, lo, hi in [(None, dummy, 2, 8), (dummy, dummy, 5, 4), (dummy, dummy, 0, 8), (dummy, dummy, 2, 9)]:
+        rc = L.srj_batch_tune_depth(1, arr, f, u, lo, hi, None, ctypes.byref(T), None)
+        assert rc == -1, (lo, hi)
+    rc = L.srj_batch_tune_depth(1, arr, dummy, dummy, 2, 8, None, None, None)
+    assert rc == -1
+    for limit in (0, -5, 1000001):
+        assert L.srj_selftest_wait_timeout(limit, None) == -1
