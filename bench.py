@@ -13,7 +13,9 @@ FP64 SRJ on the same grid as the comparator.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl srj|reference]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (a few sweeps on the full grid) on the host cores.
+workload (--ref-sweeps sweeps of the full grid per step, ~1 s) on one host
+core; the main line's cpu_baseline is the same oracle on --cpu-sweeps sweeps
+(~9 s).
 Multi-GPU (torchrun): every rank solves its own replica of the workload
 (independent problems, no collective on the data path).
 """
@@ -53,7 +55,10 @@ def parse():
     ap.add_argument("--P", type=int, default=P)
     ap.add_argument("--fp64-cycles", type=int, default=0,
                     help="cycles of the plain FP64 comparator to time (0 = run it to tolerance)")
-    ap.add_argument("--cpu-sweeps", type=int, default=4, help="oracle sweeps in the CPU baseline sample")
+    ap.add_argument("--cpu-sweeps", type=int, default=256,
+                    help="oracle sweeps in the main line's CPU baseline sample (~9 s on one core at 4096^2)")
+    ap.add_argument("--ref-sweeps", type=int, default=32,
+                    help="oracle sweeps per step of --impl reference (~1 s per step at 4096^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 3-D 512^3 and batched secondary measurements")
@@ -550,8 +555,8 @@ def batched_workload(stream, peaks=None, comparators=False):
     return out
 
 
-def oracle_sample(args):
-    """FP64 oracle sweeps on the full grid; returns (Gupdates/s, seconds, sweeps)."""
+def oracle_sample(args, sweeps):
+    """`sweeps` FP64 oracle sweeps on the full grid; returns (Gupdates/s, seconds)."""
     import numpy as np
     import oracle
     import paper_1511_04292_gb300.schedules as sch
@@ -562,9 +567,9 @@ def oracle_sample(args):
     seq = oracle.omega_sequence(row["omega"], row["order"])
     oracle.build()
     t0 = time.perf_counter()
-    oracle.steps(dims, 1.0 / (args.n + 1), seq, f, u, first=0, count=args.cpu_sweeps)
+    oracle.steps(dims, 1.0 / (args.n + 1), seq, f, u, first=0, count=sweeps)
     dt = time.perf_counter() - t0
-    return args.cpu_sweeps * args.n * args.n / dt / 1e9, dt
+    return sweeps * args.n * args.n / dt / 1e9, dt
 
 
 def run_reference(args):
@@ -573,7 +578,7 @@ def run_reference(args):
         return 0
     vals = []
     for i in range(args.warmup + args.steps):
-        g, dt = oracle_sample(args)
+        g, dt = oracle_sample(args, args.ref_sweeps)
         if i >= args.warmup:
             vals.append((g, dt))
     value = statistics.mean(v for v, _ in vals)
@@ -582,7 +587,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": "Gupdates/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d FP64 sweeps of the full %dx%d grid per step" % (args.cpu_sweeps, args.n, args.n)},
+                             "sample": "%d FP64 sweeps of the full %dx%d grid per step" % (args.ref_sweeps, args.n, args.n)},
             "e2e": {"value": value, "unit": "Gupdates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -712,7 +717,7 @@ def run_srj(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, dt = oracle_sample(args)
+        g, dt = oracle_sample(args, args.cpu_sweeps)
         sweeps_solve = stats[-1]["sweeps"]
         cpu = {"value": g, "unit": "Gupdates/s", "cores": 1, "kind": "oracle",
                "sample": "%d FP64 oracle sweeps of the full %dx%d grid (%.1f s)" % (args.cpu_sweeps, n, n, dt),

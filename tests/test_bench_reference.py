@@ -17,7 +17,7 @@ def _run(env_extra, *args):
 
 
 def test_reference_line_has_the_contract_keys():
-    r = _run({}, "--steps", "1", "--warmup", "3", "--n", "512", "--cpu-sweeps", "2")
+    r = _run({}, "--steps", "1", "--warmup", "3", "--n", "512", "--ref-sweeps", "2")
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
