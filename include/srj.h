@@ -136,7 +136,7 @@ int srj_plan_info(srj_plan_t plan, int64_t *M, double *kappa_min, double *log10_
  * srj_plan_set_temporal_depth -- number T of consecutive FP32 steps that one
  * sweep launch applies per HBM round trip (temporal blocking; T = 1 is the
  * plain one-step sweep).  2-D mixed-precision plans: T = 1..8 on register-
- * resident tiles (default 4).  3-D mixed-precision plans: T = 1..3, tiles
+ * resident tiles (default 8).  3-D mixed-precision plans: T = 1..3, tiles
  * streamed through z (default 2).  FP64 plans and plans with a mask or shift
  * accept only T = 1.  T blocked steps give the same bits as T single steps.
  * Re-captures the plan's cycle graph.

@@ -655,7 +655,7 @@ int srj_plan_create(srj_plan_t* out, int ndim, const int64_t* dims, double h, in
             cudaGetLastError();
             return bail(fail(SRJ_ERR_CUDA, "set-up of the blocked sweep failed"));
         }
-        p->tdepth = ndim == 2 ? 4 : 2;
+        p->tdepth = ndim == 2 ? 8 : 2;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) == cudaSuccess && sms > 0)
             p->sm_count = sms;

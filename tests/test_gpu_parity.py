@@ -509,7 +509,7 @@ def test_temporal_depth_rules():
     with pytest.raises(srj.SRJError):
         p3.set_temporal_depth(4)
     p2 = srj.Plan((16, 16), 0.1, [1.0], [1], None, "mixed")
-    assert p2.temporal_depth() == 4
+    assert p2.temporal_depth() == 8
     with pytest.raises(srj.SRJError):
         p2.set_temporal_depth(9)
 
