@@ -64,7 +64,9 @@ constexpr int kPhasesPerGraph = 16;
 enum { kFinInit0 = 0, kFinInit1 = 1, kFinCycle = 2 };
 
 // The step record of problem p for the coming phase (0 steps when inactive),
-// then its state after that phase's sweep.
+// then its state after that phase's sweep.  Weights past the record's n steps
+// are zero: the sweep runs T steps on every tile, and a zero-weight step leaves
+// each point's value as it is.
 __device__ __forceinline__ void prepare_and_advance(const srj::BatchProb& P, srj::BatchState& s, const float* cw,
                                                     srj::BatchArgs* args, int T) {
     srj::BatchArgs a;

@@ -151,7 +151,7 @@ struct BatchArgs {
     int nx, ny;            // interior points
     int n;                 // steps in this phase (0: inactive)
     int fresh;             // ein is identically 0
-    float c[8];            // weight / 4 of each step
+    float c[8];            // weight / 4 of each step; 0 past step n (identity steps)
 };
 
 // Problems of one grid size form a group; a group's FP32 workspaces follow each

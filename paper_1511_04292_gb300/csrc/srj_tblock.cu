@@ -36,16 +36,16 @@ constexpr int kBand = kSY / kWarps;
 // slot, so each step costs one barrier and four shared-memory accesses per lane.
 // MY: some rows of the tile lie outside 1..ny (iny[] is uniform over the warp);
 // MX: some columns lie outside 1..nx.  Those points keep their value.
+// cs[t]: weight / 4 of step t.
 template <int T, bool MY, bool MX, int W = kWarps>
 __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr)[kBand], float4* xch,
-                                           const float (&cs)[8], int n, int lane, int w, const bool (&inx)[4],
+                                           const float (&cs)[8], int lane, int w, const bool (&inx)[4],
                                            const bool (&iny)[kBand]) {
     const float two_d = 4.0f;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 m4 = make_float2(-two_d, -two_d);
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-        if (t >= n) break;  // n is uniform over the block (T when known at compile time)
         const float2 cv = make_float2(cs[t], cs[t]);
         float4* slot = xch + (t & 1) * (2 * W * 32);
         slot[(2 * w) * 32 + lane] = e[0];              // top row of this band
@@ -93,80 +93,6 @@ __device__ __forceinline__ void band_steps(float4 (&e)[kBand], const float4 (&rr
     }
 }
 
-// One tile of T-step blocking on one grid: n <= T steps with weights cs[0..n).
-// X0 / Y0: padded coordinates of the tile's first column / row.  fresh: the
-// input iterate is identically zero (start of a defect-correction cycle), so it
-// is not read.
-template <int T, int W = kWarps>
-__device__ __forceinline__ void tile_sweep(const float* __restrict__ ein, const float* __restrict__ rin,
-                                           float* __restrict__ eout, int nx, int ny, int64_t p32, int64_t rows,
-                                           const float (&cs)[8], int n, int bx, int by, bool fresh, float4* xch) {
-    constexpr int HX = T <= 4 ? 4 : 8;
-    constexpr int SY = W * kBand;  // tile rows
-    constexpr int TX = kSX - 2 * HX;
-    constexpr int TY = SY - 2 * T;
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
-    const int X0 = 1 + TX * bx - HX;
-    const int Y0 = 1 + TY * by - T;
-    const int Yw = Y0 + w * kBand;  // this warp's first row
-    // a tile whose every point is an interior grid point needs no masks
-    const bool xin = X0 >= 1 && X0 + kSX - 1 <= nx;
-    const bool yin = Y0 >= 1 && Y0 + SY - 1 <= ny;
-
-    // Band fill: float4 loads of e and r straight into registers.  The float32
-    // column of padded x is x + 3, a multiple of 4 here, so each float4 lies
-    // wholly inside or outside the buffer (rows 0..rows-1, columns 0..p32-1);
-    // outside ones read as zero.
-    const int col = X0 + 3 + 4 * lane;
-    const bool colok = col >= 0 && col + 4 <= p32;
-    float4 e[kBand], rr[kBand];
-    bool iny[kBand];
-#pragma unroll
-    for (int i = 0; i < kBand; ++i) {
-        const int64_t y = (int64_t)Yw + i;
-        e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        rr[i] = e[i];
-        if (colok && y >= 0 && y < rows) {
-            const int64_t off = y * p32 + col;
-            if (!fresh) e[i] = __ldg(reinterpret_cast<const float4*>(ein + off));
-            rr[i] = __ldg(reinterpret_cast<const float4*>(rin + off));
-        }
-        iny[i] = y >= 1 && y <= ny;
-    }
-    bool inx[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int x = X0 + 4 * lane + j;
-        inx[j] = x >= 1 && x <= nx;
-    }
-    if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
-    else if (xin)   band_steps<T, true, false, W>(e, rr, xch, cs, n, lane, w, inx, iny);
-    else if (yin)   band_steps<T, false, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
-    else            band_steps<T, true, true, W>(e, rr, xch, cs, n, lane, w, inx, iny);
-
-    // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
-    const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
-    if (lane < lane_lo || lane >= lane_hi) return;
-#pragma unroll
-    for (int i = 0; i < kBand; ++i) {
-        const int row = w * kBand + i;
-        if (row < T || row >= T + TY) continue;
-        const int y = Y0 + row;
-        if (y < 1 || y > ny) continue;
-        const int x = X0 + 4 * lane;
-        float* dst = eout + (int64_t)y * p32 + x + 3;  // 16-byte aligned
-        if (inx[0] && inx[3]) {
-            *reinterpret_cast<float4*>(dst) = e[i];
-        } else {
-            if (inx[0]) dst[0] = e[i].x;
-            if (inx[1]) dst[1] = e[i].y;
-            if (inx[2]) dst[2] = e[i].z;
-            if (inx[3]) dst[3] = e[i].w;
-        }
-    }
-}
-
 // L2 prefetch of the rows of e and of the defect that a warp will load for the
 // tile (bx, by): kBand rows of 128 floats from column X0 + 3 (512 bytes, five
 // 128-byte lines at most) per array.  Lane (i, part) covers line `part` of row i.
@@ -192,10 +118,10 @@ __device__ __forceinline__ void prefetch_tile_l2(const float* ein, const float* 
     }
 }
 
-// Single grid, n = T steps per launch.  Same tile as tile_sweep; interior
-// tiles (the vast majority) load and store without bounds checks.  (Kept as its
-// own body: routed through tile_sweep, this form costs the compiler hundreds of
-// bytes of register spills.)  PF: after issuing its own loads, each block
+// Single grid, T steps per launch.  Block (bx, by) owns the tile whose first
+// column / row has padded coordinates X0 = 1 + TX bx - HX, Y0 = 1 + TY by - T;
+// interior tiles (the vast majority) load and store without bounds checks.
+// PF: after issuing its own loads, each block
 // prefetches into L2 the rows of the tile pf_dist blocks further on in launch
 // order (the tile that starts on a multiprocessor when a resident block ends),
 // so that the next wave's loads are served from L2 while this wave computes.
@@ -254,10 +180,10 @@ k_sweep_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, flo
         const int x = X0 + 4 * lane + j;
         inx[j] = x >= 1 && x <= g.nx;
     }
-    if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-    else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-    else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-    else            band_steps<T, true, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+    if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+    else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+    else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+    else            band_steps<T, true, true, W>(e, rr, xch, steps.c, lane, w, inx, iny);
 
     // store the centre: rows T .. T+TY-1, columns HX .. HX+TX-1 of the tile
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
@@ -423,10 +349,10 @@ k_sweep_f32_tbq(const float* __restrict__ ein, const float* __restrict__ rin, fl
         }
         const bool xin = X0 >= 1 && X0 + kSX - 1 <= g.nx;
         const bool yin = Y0 >= 1 && Y0 + SY - 1 <= g.ny;
-        if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
-        else            band_steps<T, true, true, W>(e, rr, xch, steps.c, T, lane, w, inx, iny);
+        if (xin && yin) band_steps<T, false, false, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+        else if (xin)   band_steps<T, true, false, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+        else if (yin)   band_steps<T, false, true, W>(e, rr, xch, steps.c, lane, w, inx, iny);
+        else            band_steps<T, true, true, W>(e, rr, xch, steps.c, lane, w, inx, iny);
         const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
         if (lane >= lane_lo && lane < lane_hi) {
             if (xin && yin) {
@@ -465,7 +391,11 @@ k_sweep_f32_tbq(const float* __restrict__ ein, const float* __restrict__ rin, fl
 // Batched form: one launch covers the tiles of every problem of a batch; each
 // block finds its problem in the tile table and advances it by
 // n = min(T, M - k) steps of its own cycle order.  Problems that have finished
-// are skipped.
+// are skipped.  Every tile runs T steps: the record's weights past step n are
+// zero, and a step with weight zero returns each point's value unchanged
+// (fma(0, y, e) = e for finite y), so the tile holds the same values as after n
+// steps.  A runtime step count in the unrolled step loop instead made the
+// compiler spill several hundred bytes of registers (-Xptxas -v).
 template <int T>
 __global__ void __launch_bounds__(kWarps * 32, 2)
 k_batch_sweep_tb(const int4* __restrict__ tiles, const BatchArgs* __restrict__ args) {
@@ -520,10 +450,10 @@ k_batch_sweep_tb(const int4* __restrict__ tiles, const BatchArgs* __restrict__ a
         const int x = X0 + 4 * lane + j;
         inx[j] = x >= 1 && x <= A.nx;
     }
-    if (xin && yin) band_steps<T, false, false>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
-    else if (xin)   band_steps<T, true, false>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
-    else if (yin)   band_steps<T, false, true>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
-    else            band_steps<T, true, true>(e, rr, xch, Ap->c, n, lane, w, inx, iny);
+    if (xin && yin) band_steps<T, false, false>(e, rr, xch, Ap->c, lane, w, inx, iny);
+    else if (xin)   band_steps<T, true, false>(e, rr, xch, Ap->c, lane, w, inx, iny);
+    else if (yin)   band_steps<T, false, true>(e, rr, xch, Ap->c, lane, w, inx, iny);
+    else            band_steps<T, true, true>(e, rr, xch, Ap->c, lane, w, inx, iny);
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
     if (lane < lane_lo || lane >= lane_hi) return;
     if (xin && yin) {
@@ -562,7 +492,9 @@ k_batch_sweep_tb(const int4* __restrict__ tiles, const BatchArgs* __restrict__ a
 // record first, as k_batch_sweep_tb does, puts a dependent load ahead of every
 // tile; on full-grid tiles that cost about a fifth of the sweep time.  The
 // input correction is read even at a cycle start (zero start) and then
-// replaced by zeros, which is what the tile-list kernel computes.
+// replaced by zeros, which is what the tile-list kernel computes.  Like the
+// tile-list kernel it always runs T steps, with zero weights past the record's
+// step count.
 template <int T>
 __global__ void __launch_bounds__(kWarps * 32, 2)
 k_batch_sweep_grp(const BatchGroups G, float* __restrict__ pool, const BatchArgs* __restrict__ args, int parity) {
@@ -638,14 +570,13 @@ k_batch_sweep_grp(const BatchGroups G, float* __restrict__ pool, const BatchArgs
     }
     __syncthreads();  // the weights in csh
     if (xin && yin) {
-        if (n == T) band_steps<T, false, false>(e, rr, xch, csh, T, lane, w, inx, iny);
-        else        band_steps<T, false, false>(e, rr, xch, csh, n, lane, w, inx, iny);
+        band_steps<T, false, false>(e, rr, xch, csh, lane, w, inx, iny);
     } else if (xin) {
-        band_steps<T, true, false>(e, rr, xch, csh, n, lane, w, inx, iny);
+        band_steps<T, true, false>(e, rr, xch, csh, lane, w, inx, iny);
     } else if (yin) {
-        band_steps<T, false, true>(e, rr, xch, csh, n, lane, w, inx, iny);
+        band_steps<T, false, true>(e, rr, xch, csh, lane, w, inx, iny);
     } else {
-        band_steps<T, true, true>(e, rr, xch, csh, n, lane, w, inx, iny);
+        band_steps<T, true, true>(e, rr, xch, csh, lane, w, inx, iny);
     }
     const int lane_lo = HX / 4, lane_hi = (HX + TX) / 4;
     if (lane < lane_lo || lane >= lane_hi) return;
