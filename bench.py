@@ -68,7 +68,8 @@ def parse():
                          "solve of the batched workload, and exit; prints no JSON")
     ap.add_argument("--count", type=int, default=4)
     ap.add_argument("--ndim", type=int, default=2, choices=[2, 3], help="kernel-case: grid dimension (n^ndim points)")
-    ap.add_argument("--T", type=int, default=None, help="kernel-case f32: temporal depth (default: the plan's)")
+    ap.add_argument("--T", type=int, default=None,
+                    help="kernel-case f32 / batch: temporal depth (default: the plan's / the depth tuner's)")
     ap.add_argument("--variant", type=int, default=None, help="kernel-case f32: blocked sweep variant (0..3)")
     return ap.parse_args()
 
@@ -81,7 +82,7 @@ def run_kernel_case(args):
     torch.cuda.set_device(0)
     dims = (n,) * args.ndim
     if args.kernel_case == "batch":
-        res = batched_workload(torch.cuda.current_stream())
+        res = batched_workload(torch.cuda.current_stream(), depth=args.T)
         print("kernel case batch:", res)
         return 0
     if args.kernel_case == "sphmix":  # one mixed-precision cycle of the Sect. 5.2 test (blocked FP32 sweeps)
@@ -492,12 +493,13 @@ def secondary_workloads(stream, peaks, T, variant):
     return out
 
 
-def batched_workload(stream, peaks=None, comparators=False):
+def batched_workload(stream, peaks=None, comparators=False, depth=None):
     """One timed solve of the batched workload: 256 problems, n in {64..1024},
     P in 5..10, mixed precision, tol 1e-10 (after one untimed solve).  With
     comparators: the same problems solved one mixed plan at a time (measured),
     and by plain FP64 plans (each problem's FP64 cycle timed, times the cycles
-    that problem needed in the batch)."""
+    that problem needed in the batch).  depth: a fixed temporal depth instead
+    of the depth tuner's (for profiling runs)."""
     import torch
     import paper_1511_04292_gb300 as srj
     import srj_workloads as W
@@ -509,7 +511,10 @@ def batched_workload(stream, peaks=None, comparators=False):
         fh, uh = W.random_smooth_problem_2d(nn, seed)
         probs.append(dict(dims=(nn, nn), h=1.0 / (nn + 1), omega=row["omega"], q=row["q"], order=row["order"]))
         fs.append(torch.from_numpy(fh).cuda()); u0s.append(torch.from_numpy(uh).cuda())
-    tuned_T, tuned_ms = srj.Batch.tune_depth(probs, fs, u0s, 4, 8, stream=stream)
+    if depth is None:
+        tuned_T, tuned_ms = srj.Batch.tune_depth(probs, fs, u0s, 4, 8, stream=stream)
+    else:
+        tuned_T, tuned_ms = depth, float("nan")
     batch = srj.Batch(probs, temporal_depth=tuned_T)
     us = [x.clone() for x in u0s]
     batch.solve(fs, us, 1e-10, 500)  # warm-up
@@ -520,8 +525,9 @@ def batched_workload(stream, peaks=None, comparators=False):
     upd = sum(s_["sweeps"] * nn * nn for s_, (nn, _, _) in zip(stats, specs))
     line = {"time_to_tol_s": ms / 1e3, "gupdates_per_s": upd / (ms / 1e3) / 1e9, "status": rc,
             "max_cycles": max(s_["cycles"] for s_ in stats), "points": sum(nn * nn for nn, _, _ in specs),
-            "temporal_depth": T, "depth_tuner": "srj_batch_tune_depth over T = 4..8 (one cycle of every problem "
-                                                "each): T = %d, %.1f ms per cycle" % (tuned_T, tuned_ms),
+            "temporal_depth": T, "depth_tuner": ("srj_batch_tune_depth over T = 4..8 (one cycle of every problem "
+                                                 "each): T = %d, %.1f ms per cycle" % (tuned_T, tuned_ms))
+                                                if depth is None else "not run: depth fixed at %d" % depth,
             "device_ms": dms,
             "max_final_rel_residual": max(s_["rel_res"] for s_ in stats)}
     if peaks is not None:

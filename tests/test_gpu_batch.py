@@ -52,6 +52,32 @@ def test_batch_matches_single_plan_solves_bit_for_bit():
         assert l2 <= 1e-10 * r0 * (1 + 1e-9)
 
 
+def test_more_problems_than_one_step_block():
+    """300 problems: the per-phase step kernel (one thread per problem, 256
+    per block) runs on more than one block, and the row blocks due at a cycle
+    end come from both.  Sampled problems equal their single-plan solves bit
+    for bit; every residual is re-checked by the oracle."""
+    rng = np.random.default_rng(17)
+    specs = [(64, int(P), 2000 + i) for i, P in enumerate(rng.integers(5, 11, size=300))]
+    probs, fs, u0s = zip(*[_problem(*s) for s in specs])
+    T = 8
+    batch = srj.Batch(list(probs), temporal_depth=T)
+    ud = [torch.from_numpy(u).cuda() for u in u0s]
+    stats, ms, rc = batch.solve([torch.from_numpy(f).cuda() for f in fs], ud, 1e-10, 200)
+    assert rc == 0
+    for i in range(0, len(specs), 23):
+        n, P, _ = specs[i]
+        plan = srj.Plan.from_table((n, n), P, "mixed")
+        plan.set_temporal_depth(T)
+        ref = torch.from_numpy(u0s[i]).cuda()
+        st1 = plan.solve(torch.from_numpy(fs[i]).cuda(), ref, 1e-10, 200)
+        assert stats[i]["cycles"] == st1["cycles"] and torch.equal(ud[i], ref), (i, P)
+    for (n, P, _), pr, f, u0, u in zip(specs, probs, fs, u0s, ud):
+        r0, _ = oracle.residual((n, n), pr["h"], f, u0)
+        l2, _ = oracle.residual((n, n), pr["h"], f, u.cpu().numpy())
+        assert l2 <= 1e-10 * r0 * (1 + 1e-9)
+
+
 def test_batch_ragged_sizes_and_own_orders():
     """Non-square and non-table grids with schedules from the oracle's solver and
     the library's own order (order=None)."""
