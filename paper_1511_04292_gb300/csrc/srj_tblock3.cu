@@ -18,8 +18,10 @@
 // T single-step launches.
 //
 // The block is persistent (one per SM: the rings take 176 KB for T = 2, 224 KB
-// for T = 3) and walks work items (tile, z segment) round robin; a segment of
-// 64 output planes costs 2T extra plane iterations of pipeline fill.
+// for T = 3) and walks work items (tile, z segment) round robin; a segment
+// costs 2T extra plane iterations of pipeline fill, so the launcher picks the
+// segment length (about 32 to 128 planes) for which the busiest block walks the
+// fewest plane iterations (64 at 512^3 with T = 2, 86 with T = 3).
 #include "srj_internal.h"
 
 #include <atomic>
@@ -35,7 +37,7 @@ constexpr int kWarps = 16;
 constexpr int kY = 2 * kWarps;          // tile rows: 2 per warp
 constexpr int kHX = 4;                  // x halo: T <= 4 steps rounded up to a float4
 constexpr int kTX = kX - 2 * kHX;       // 120 centre columns
-constexpr int kZSeg = 64;               // output planes per work item
+constexpr int kZSegMin = 32, kZSegMax = 128;  // output planes per work item (z segment), chosen per grid
 constexpr int kPlane = kY * 32;         // float4 per plane tile
 template <int T> struct Cfg {
     static constexpr int kD = 2;                     // planes loaded ahead of use (3 measured no faster)
@@ -108,15 +110,123 @@ __device__ __forceinline__ void stage_rows(const float4 (&bk)[2], const float4 (
     }
 }
 
+// One work item: the tile whose first column / row has padded coordinates X0 /
+// Y0, output planes zs .. ze-1, all T stages.
+template <int T>
+__device__ __forceinline__ void run_item(const float* __restrict__ ein, const float* __restrict__ rin,
+                                         float* __restrict__ eout, const Geom& g, const TbSteps& steps, int X0, int Y0,
+                                         int zs, int ze, float4* E, float4* R, float4* L, int lane, int j0, int jup,
+                                         int jdn) {
+    using C = Cfg<T>;
+    constexpr int kERing = C::kERing;
+    const int niter = ze - zs + 2 * T;     // planes zs-T .. ze-1+T
+    const int col = X0 + 3 + 4 * lane;     // multiple of 4: each float4 wholly in or out of a row
+    const bool colok = col >= 0 && col + 4 <= g.p32;
+    bool inx[4], iny[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int x = X0 + 4 * lane + q;
+        inx[q] = x >= 1 && x <= g.nx;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int y = Y0 + j0 + k;
+        iny[k] = y >= 1 && y <= g.ny;
+    }
+    // plane loads of iteration i (plane zs - T + i): this thread's two rows
+    auto issue = [&](int i) {
+        if (i < niter) {
+            const int p = zs - T + i;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int y = Y0 + j0 + k;
+                const bool ok = colok && p >= 0 && p <= g.nz + 1 && y >= 0 && y <= g.ny + 1;
+                const int64_t off = ok ? (int64_t)p * g.plane32 + (int64_t)y * g.p32 + col : 0;
+                cp_async16(&E[(i % kERing) * kPlane + (j0 + k) * 32 + lane], ein + off, ok ? 16u : 0u);
+                cp_async16(&R[(i % C::kRRing) * kPlane + (j0 + k) * 32 + lane], rin + off, ok ? 16u : 0u);
+            }
+        }
+        cp_async_commit();  // possibly empty: keeps one group per iteration
+    };
+#pragma unroll
+    for (int d = 0; d < C::kD; ++d) issue(d);
+    // this thread's rows of the planes still needed: lv_bk / lv_cc[s] = level s on planes p-s-2 / p-s-1
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 lv_bk[T][2], lv_cc[T][2];
+#pragma unroll
+    for (int s = 0; s < T; ++s) {
+        lv_bk[s][0] = lv_bk[s][1] = z4;
+        lv_cc[s][0] = lv_cc[s][1] = z4;
+    }
+    for (int i = 0; i < niter; ++i) {
+        cp_async_wait_pending<C::kD - 1>();  // this thread's loads of iteration i have landed
+        __syncthreads();    // ... and everyone's; iteration i-1 is fully done
+        issue(i + C::kD);   // into slots no longer read
+        const int p = zs - T + i;
+        float4 fr[2];       // level s-1 on plane p-s+1: the stage's front plane
+        const float4* Ep = E + (i % kERing) * kPlane;
+        fr[0] = Ep[j0 * 32 + lane];
+        fr[1] = Ep[(j0 + 1) * 32 + lane];
+#pragma unroll
+        for (int s = 1; s <= T; ++s) {
+            float4 out[2];
+            const bool live = i >= 2 * s;
+            if (live) {
+                const int q = p - s;  // plane of the level-s result
+                // the centre plane's rows of the neighbouring warps, published last iteration
+                const float4* Nc = (s == 1) ? E + ((i + kERing - 1) % kERing) * kPlane
+                                            : L + ((s - 2) * 2 + ((i + 1) & 1)) * kPlane;
+                const float4* Rq = R + ((i + C::kRRing - s) % C::kRRing) * kPlane;
+                float4 rr[2];
+                rr[0] = Rq[j0 * 32 + lane];
+                rr[1] = Rq[(j0 + 1) * 32 + lane];
+                stage_rows(lv_bk[s - 1], lv_cc[s - 1], fr, Nc[jup * 32 + lane], Nc[jdn * 32 + lane], rr,
+                           steps.c[s - 1], lane, q < 1 || q > g.nz, inx, iny, out);
+                if (s < T) {
+                    float4* Lw = L + ((s - 1) * 2 + (i & 1)) * kPlane;
+                    Lw[j0 * 32 + lane] = out[0];
+                    Lw[(j0 + 1) * 32 + lane] = out[1];
+                } else if (lane >= kHX / 4 && lane < (kHX + kTX) / 4) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int j = j0 + k;
+                        const int y = Y0 + j;
+                        if (j < C::kHY || j >= C::kHY + C::kTY || y < 1 || y > g.ny) continue;
+                        const int x = X0 + 4 * lane;
+                        float* dst = eout + (int64_t)q * g.plane32 + (int64_t)y * g.p32 + x + 3;  // 16-B aligned
+                        if (inx[0] && inx[3]) {
+                            *reinterpret_cast<float4*>(dst) = out[k];
+                        } else {
+                            if (inx[0]) dst[0] = out[k].x;
+                            if (inx[1]) dst[1] = out[k].y;
+                            if (inx[2]) dst[2] = out[k].z;
+                            if (inx[3]) dst[3] = out[k].w;
+                        }
+                    }
+                }
+            }
+            // rotate level s-1: its planes advance by one
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                lv_bk[s - 1][k] = lv_cc[s - 1][k];
+                lv_cc[s - 1][k] = fr[k];
+                if (s < T && live) fr[k] = out[k];
+            }
+            if (!live) break;  // later stages start later (uniform over the block)
+        }
+    }
+}
+
+// Persistent blocks walk the work items (tile, z segment of zseg output planes)
+// round robin.
 template <int T>
 __global__ void __launch_bounds__(kWarps * 32, 1)
 k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, float* __restrict__ eout, Geom g,
-                TbSteps steps, int tiles_x, int tiles_y, int nseg) {
+                TbSteps steps, int tiles_x, int tiles_y, int nseg, int zseg) {
     using C = Cfg<T>;
     extern __shared__ float4 smem[];
-    constexpr int kERing = C::kERing;
     float4* E = smem;                          // [kERing][kPlane]   level-0 e planes
-    float4* R = E + kERing * kPlane;           // [kRRing][kPlane]   defect planes
+    float4* R = E + C::kERing * kPlane;        // [kRRing][kPlane]   defect planes
     float4* L = R + C::kRRing * kPlane;        // [T-1][2][kPlane]   published level planes
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j0 = 2 * w;                      // this warp's rows of the tile
@@ -127,103 +237,8 @@ k_sweep3_f32_tb(const float* __restrict__ ein, const float* __restrict__ rin, fl
         const int by = (item / tiles_x) % tiles_y;
         const int sg = item / (tiles_x * tiles_y);
         const int X0 = 1 + kTX * bx - kHX, Y0 = 1 + C::kTY * by - C::kHY;
-        const int zs = 1 + sg * kZSeg, ze = min(zs + kZSeg, g.nz + 1);
-        const int niter = ze - zs + 2 * T;     // planes zs-T .. ze-1+T
-        const int col = X0 + 3 + 4 * lane;     // multiple of 4: each float4 wholly in or out of a row
-        const bool colok = col >= 0 && col + 4 <= g.p32;
-        bool inx[4], iny[2];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x = X0 + 4 * lane + q;
-            inx[q] = x >= 1 && x <= g.nx;
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int y = Y0 + j0 + k;
-            iny[k] = y >= 1 && y <= g.ny;
-        }
-        // plane loads of iteration i (plane zs - T + i): this thread's two rows
-        auto issue = [&](int i) {
-            if (i < niter) {
-                const int p = zs - T + i;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int y = Y0 + j0 + k;
-                    const bool ok = colok && p >= 0 && p <= g.nz + 1 && y >= 0 && y <= g.ny + 1;
-                    const int64_t off = ok ? (int64_t)p * g.plane32 + (int64_t)y * g.p32 + col : 0;
-                    cp_async16(&E[(i % kERing) * kPlane + (j0 + k) * 32 + lane], ein + off, ok ? 16u : 0u);
-                    cp_async16(&R[(i % C::kRRing) * kPlane + (j0 + k) * 32 + lane], rin + off, ok ? 16u : 0u);
-                }
-            }
-            cp_async_commit();  // possibly empty: keeps one group per iteration
-        };
-#pragma unroll
-        for (int d = 0; d < C::kD; ++d) issue(d);
-        // this thread's rows of the planes still needed: lv_bk / lv_cc[s] = level s on planes p-s-2 / p-s-1
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 lv_bk[T][2], lv_cc[T][2];
-#pragma unroll
-        for (int s = 0; s < T; ++s) {
-            lv_bk[s][0] = lv_bk[s][1] = z4;
-            lv_cc[s][0] = lv_cc[s][1] = z4;
-        }
-        for (int i = 0; i < niter; ++i) {
-            cp_async_wait_pending<C::kD - 1>();  // this thread's loads of iteration i have landed
-            __syncthreads();    // ... and everyone's; iteration i-1 is fully done
-            issue(i + C::kD);   // into slots no longer read
-            const int p = zs - T + i;
-            float4 fr[2];       // level s-1 on plane p-s+1: the stage's front plane
-            const float4* Ep = E + (i % kERing) * kPlane;
-            fr[0] = Ep[j0 * 32 + lane];
-            fr[1] = Ep[(j0 + 1) * 32 + lane];
-#pragma unroll
-            for (int s = 1; s <= T; ++s) {
-                float4 out[2];
-                const bool live = i >= 2 * s;
-                if (live) {
-                    const int q = p - s;  // plane of the level-s result
-                    // the centre plane's rows of the neighbouring warps, published last iteration
-                    const float4* Nc = (s == 1) ? E + ((i + kERing - 1) % kERing) * kPlane
-                                                : L + ((s - 2) * 2 + ((i + 1) & 1)) * kPlane;
-                    const float4* Rq = R + ((i + C::kRRing - s) % C::kRRing) * kPlane;
-                    float4 rr[2];
-                    rr[0] = Rq[j0 * 32 + lane];
-                    rr[1] = Rq[(j0 + 1) * 32 + lane];
-                    stage_rows(lv_bk[s - 1], lv_cc[s - 1], fr, Nc[jup * 32 + lane], Nc[jdn * 32 + lane], rr,
-                               steps.c[s - 1], lane, q < 1 || q > g.nz, inx, iny, out);
-                    if (s < T) {
-                        float4* Lw = L + ((s - 1) * 2 + (i & 1)) * kPlane;
-                        Lw[j0 * 32 + lane] = out[0];
-                        Lw[(j0 + 1) * 32 + lane] = out[1];
-                    } else if (lane >= kHX / 4 && lane < (kHX + kTX) / 4) {
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            const int j = j0 + k;
-                            const int y = Y0 + j;
-                            if (j < C::kHY || j >= C::kHY + C::kTY || y < 1 || y > g.ny) continue;
-                            const int x = X0 + 4 * lane;
-                            float* dst = eout + (int64_t)q * g.plane32 + (int64_t)y * g.p32 + x + 3;  // 16-B aligned
-                            if (inx[0] && inx[3]) {
-                                *reinterpret_cast<float4*>(dst) = out[k];
-                            } else {
-                                if (inx[0]) dst[0] = out[k].x;
-                                if (inx[1]) dst[1] = out[k].y;
-                                if (inx[2]) dst[2] = out[k].z;
-                                if (inx[3]) dst[3] = out[k].w;
-                            }
-                        }
-                    }
-                }
-                // rotate level s-1: its planes advance by one
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    lv_bk[s - 1][k] = lv_cc[s - 1][k];
-                    lv_cc[s - 1][k] = fr[k];
-                    if (s < T && live) fr[k] = out[k];
-                }
-                if (!live) break;  // later stages start later (uniform over the block)
-            }
-        }
+        const int zs = 1 + sg * zseg, ze = min(zs + zseg, g.nz + 1);
+        run_item<T>(ein, rin, eout, g, steps, X0, Y0, zs, ze, E, R, L, lane, j0, jup, jdn);
         cp_async_wait_all();
         __syncthreads();  // the next item's first loads reuse ring slots
     }
@@ -250,14 +265,31 @@ int tb3_max_steps() { return 3; }
 cudaError_t launch_sweep3_f32_tb(const Geom& g, const float* ein, const float* rin, float* eout, const TbSteps& steps,
                                  int blocks, cudaStream_t s) {
     if (g.nd != 3 || blocks < 1 || steps.T < 2 || steps.T > 3) return cudaErrorInvalidValue;
-    const int TY = kY - 2 * steps.T;
-    const int tx = (g.nx + kTX - 1) / kTX, ty = (g.ny + TY - 1) / TY, ns = (g.nz + kZSeg - 1) / kZSeg;
-    const int items = tx * ty * ns;
-    const unsigned grid = (unsigned)std::min(blocks, items);
-    if (steps.T == 2)
-        k_sweep3_f32_tb<2><<<grid, kWarps * 32, Cfg<2>::kSmem, s>>>(ein, rin, eout, g, steps, tx, ty, ns);
+    const int T = steps.T;
+    const int TY = kY - 2 * T;
+    const int tx = (g.nx + kTX - 1) / kTX, ty = (g.ny + TY - 1) / TY;
+    // z segments: the count whose busiest block walks the fewest plane iterations,
+    // rounds x (segment + 2T warm-up planes), for segments of about 32 to 128 planes
+    const int64_t tiles = (int64_t)tx * ty;
+    const int ns_lo = std::max(1, (g.nz + kZSegMax - 1) / kZSegMax);
+    const int ns_hi = std::max(ns_lo, (g.nz + kZSegMin - 1) / kZSegMin);
+    int ns = 1, zseg = g.nz;
+    int64_t best = -1;
+    for (int n = ns_lo; n <= ns_hi; ++n) {
+        const int z = (g.nz + n - 1) / n;         // segments of z planes (the last one may be shorter) ...
+        const int nz_seg = (g.nz + z - 1) / z;    // ... and how many of them cover the grid
+        const int64_t items = tiles * nz_seg;
+        const int64_t grid = std::min<int64_t>(blocks, items);
+        const int64_t cost = (items + grid - 1) / grid * (z + 2 * T);
+        if (best < 0 || cost < best) { best = cost; ns = nz_seg; zseg = z; }
+    }
+    const int64_t items = tiles * ns;
+    if (items > INT32_MAX) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks, items);
+    if (T == 2)
+        k_sweep3_f32_tb<2><<<grid, kWarps * 32, Cfg<2>::kSmem, s>>>(ein, rin, eout, g, steps, tx, ty, ns, zseg);
     else
-        k_sweep3_f32_tb<3><<<grid, kWarps * 32, Cfg<3>::kSmem, s>>>(ein, rin, eout, g, steps, tx, ty, ns);
+        k_sweep3_f32_tb<3><<<grid, kWarps * 32, Cfg<3>::kSmem, s>>>(ein, rin, eout, g, steps, tx, ty, ns, zseg);
     return cudaGetLastError();
 }
 

@@ -363,16 +363,19 @@ def test_full_size_workload2_mixed_solve():
 
 def test_full_size_workload3_mixed_solve():
     """Workload 3 at full size (512^3, 8 Gaussian blobs, P = 12, mixed, tol 1e-9)
-    in the launch configuration the benchmark times (two FP32 steps per 3-D
-    blocked launch): the oracle's residual of the returned u is within
-    tolerance; at this size the blocked steps give the bits of single steps; and
-    one FP32 step agrees with the oracle within the rounding bound on sampled z
-    planes (first, last, and both sides of a 64-plane segment boundary)."""
+    in the launch configuration the benchmark times (the autotuner's temporal
+    depth): the oracle's residual of the returned u is within tolerance; at this
+    size the blocked steps give the bits of single steps; and one FP32 step
+    agrees with the oracle within the rounding bound on sampled z planes
+    (first, last, and both sides of the boundaries between the first two z
+    segments for both blocked depths: 64 planes long with T = 2, 86 with T = 3)."""
     n = 512
     dims = (n, n, n)
     f, u0 = W.gaussian_blobs_3d(n, 3)
     plan = srj.Plan.from_table(dims, 12, "mixed")
     assert plan.temporal_depth() == 2
+    T, _ = plan.autotune()
+    assert T in (1, 2, 3) and plan.temporal_depth() == T
     fd = dev(f)
     ud = dev(u0)
     st = plan.solve(fd, ud, 1e-9, 200)
@@ -381,17 +384,17 @@ def test_full_size_workload3_mixed_solve():
     r0, _ = oracle.residual(dims, plan.h, f, u0)
     l2, _ = oracle.residual(dims, plan.h, f, u)
     assert l2 <= 1e-9 * r0 * (1 + 1e-9), (l2 / r0, st)
-    # blocked (depth 2) against single steps, from u0, even and ragged counts
-    for first, count in [(0, 8), (3, 7)]:
-        plan.set_temporal_depth(2)
+    # blocked (both depths) against single steps, from u0, even and ragged counts
+    for first, count, depth in [(0, 8, 2), (3, 7, 2), (0, 12, 3), (5, 7, 3)]:
+        plan.set_temporal_depth(depth)
         got = dev(u0)
         plan.steps(fd, got, first, count)
         plan.set_temporal_depth(1)
         ref = dev(u0)
         plan.steps(fd, ref, first, count)
-        assert torch.equal(got, ref), (first, count)
+        assert torch.equal(got, ref), (first, count, depth)
         del got, ref
-    plan.set_temporal_depth(2)
+    plan.set_temporal_depth(T)
     # one step of the largest weight on the converged field, against the oracle on z slabs
     row = srj.schedules.lookup(3, n, 12)
     k = int(np.argmax(row["omega"][row["order"]]))
@@ -402,7 +405,7 @@ def test_full_size_workload3_mixed_solve():
     del ud2
     h = plan.h
     c = w / 6
-    for z in (1, 2, 64, 65, 257, n - 1, n):
+    for z in (1, 2, 64, 65, 86, 87, 257, n - 1, n):
         sl = slice(z - 1, z + 2)
         u32 = np.ascontiguousarray(u[sl]).astype(np.float32).astype(np.float64)
         f32 = (h * h * np.ascontiguousarray(f[sl])).astype(np.float32).astype(np.float64) / (h * h)
@@ -441,9 +444,10 @@ def test_blocked_fp32_sweep_bit_identical_to_single_steps(dims):
 @pytest.mark.parametrize("dims", [(37, 23, 19), (130, 67, 70), (1, 1, 1), (5, 300, 3), (129, 29, 65), (250, 2, 130)])
 def test_blocked_fp32_sweep_3d_bit_identical_to_single_steps(dims):
     """3-D temporal blocking (T = 2 or 3 steps per launch, tiles streamed through
-    z in segments of 64 planes) must give exactly the bits of single-step
-    launches, for step counts that are not multiples of T, on grids ragged
-    against the tile centre and spanning more than one z segment."""
+    z segments whose length the launcher picks per grid) must give exactly the
+    bits of single-step launches, for step counts that are not multiples of T,
+    on grids ragged against the tile centre and spanning more than one z
+    segment."""
     omega, q, order = small_schedule(dims, 4)
     h = 1.0 / (max(dims) + 1)
     f, u = random_problem(dims, 43)
