@@ -383,8 +383,13 @@ cudaError_t launch_scale_source(const Geom& g, double h2, const double* f, doubl
 cudaError_t launch_sweep_f64(const Geom& g, const double* uin, double* uout, const double* b, double c,
                              cudaStream_t s, double two_d, const unsigned char* mask, bool fused) {
     if (two_d == 0.0) two_d = 2.0 * g.nd;
-    dim3 blk(64, 4, 1);
-    dim3 grd((g.nx + 63) / 64, (g.ny + 3) / 4, g.nd == 3 ? (unsigned)std::min(g.nz, 65535) : 1u);
+    // Each FP64 update costs the multiprocessor's FP64 pipe (2 instructions per
+    // clock), so a small grid is spread over more multiprocessors with blocks
+    // of 64 threads instead of 256.
+    const int64_t pts = (int64_t)g.nx * g.ny * (g.nd == 3 ? g.nz : 1);
+    const dim3 blk = pts < (int64_t{1} << 17) ? dim3(32, 2, 1) : dim3(64, 4, 1);
+    dim3 grd((g.nx + blk.x - 1) / blk.x, (g.ny + blk.y - 1) / blk.y,
+             g.nd == 3 ? (unsigned)std::min(g.nz, 65535) : 1u);
     if (fused) {
         if (g.nd == 3) k_sweep_f64<3, true><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
         else           k_sweep_f64<2, true><<<grd, blk, 0, s>>>(g, uin, uout, b, c, two_d, mask);
